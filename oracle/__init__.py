@@ -1,0 +1,124 @@
+"""ctypes wrapper of the sequential CPU oracle (rr_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg are the only users of this package. The CUDA library and its
+Python binding never import it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rr_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+OK, INFEASIBLE, ERR_ARG, ERR_CAPACITY, ERR_NOMEM, ERR_BUG = 0, 1, -1, -2, -5, -6
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (portable flags only)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "rr_oracle.h"))):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-Wextra", "-shared", "-fPIC",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i32, i64 = ctypes.c_int, ctypes.c_int64
+        L.rro_window.argtypes = [P, i32, i32, i32]
+        L.rro_window.restype = i32
+        L.rro_split.argtypes = [P, i32, P, i32, P, i32, i32, i32, i32, P]
+        L.rro_split.restype = i32
+        L.rro_plan.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, i64, P]
+        L.rro_plan.restype = i32
+        L.rro_batch.argtypes = [P, i64, i32, i32, P, i64, P, i64, P, P]
+        L.rro_batch.restype = i32
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None and a.size else None
+
+
+def window(s, r0: int, h: int) -> int:
+    s = np.ascontiguousarray(s, dtype=np.int32)
+    return lib().rro_window(_ptr(s) or ctypes.c_void_p(1), len(s), r0, h) if len(s) else (
+        0 if h == 0 else -1)
+
+
+def split(mand, top, bot, x: int, r0: int, h: int):
+    mand = np.ascontiguousarray(mand, dtype=np.int32)
+    top = np.ascontiguousarray(top, dtype=np.int32)
+    bot = np.ascontiguousarray(bot, dtype=np.int32)
+    cost = ctypes.c_int64(0)
+    a = lib().rro_split(_ptr(mand), len(mand), _ptr(top), len(top), _ptr(bot), len(bot),
+                        x, r0, h, ctypes.byref(cost))
+    return a, cost.value
+
+
+class Plan:
+    def __init__(self, status, moves, sigma, events):
+        self.status = status
+        self.moves = moves          # (k, 4) int32: src_row, src_col, dst_row, dst_col
+        self.sigma = sigma          # (n,) int32 surplus after the column phase
+        self.events = events        # (e, 5) int32: case, donor, receiver, x, a
+
+
+def plan(grid: np.ndarray, rect, with_trace: bool = False) -> Plan:
+    grid = np.ascontiguousarray(grid, dtype=np.uint8)
+    m, n = grid.shape
+    r0, c0, r1, c1 = (int(v) for v in rect)
+    nm = ctypes.c_int64(0)
+    ne = ctypes.c_int64(0)
+    sigma = np.zeros(n, dtype=np.int32)
+    cap = 0
+    cap_ev = 2 * n + 2 if with_trace else 0
+    events = np.zeros((max(cap_ev, 1), 5), dtype=np.int32)
+    while True:
+        moves = np.zeros((max(cap, 1), 4), dtype=np.int32)
+        st = lib().rro_plan(_ptr(grid), m, n, r0, c0, r1, c1, _ptr(moves), cap,
+                            ctypes.byref(nm), _ptr(sigma), _ptr(events) if with_trace else None,
+                            cap_ev, ctypes.byref(ne))
+        if st == ERR_CAPACITY:
+            cap = nm.value
+            continue
+        break
+    if st not in (OK, INFEASIBLE):
+        raise RuntimeError(f"oracle rro_plan failed with status {st}")
+    return Plan(st, moves[: nm.value].copy(), sigma,
+                events[: ne.value].copy() if with_trace else None)
+
+
+def batch(moves: np.ndarray, m: int, n: int):
+    """Returns (ops (b, 3) int32: dir, first, count; members (s,) int32)."""
+    moves = np.ascontiguousarray(moves, dtype=np.int32).reshape(-1, 4)
+    no = ctypes.c_int64(0)
+    nmem = ctypes.c_int64(0)
+    cap_o = cap_m = 0
+    while True:
+        ops = np.zeros((max(cap_o, 1), 3), dtype=np.int32)
+        mem = np.zeros(max(cap_m, 1), dtype=np.int32)
+        st = lib().rro_batch(_ptr(moves), len(moves), m, n, _ptr(ops), cap_o, _ptr(mem), cap_m,
+                             ctypes.byref(no), ctypes.byref(nmem))
+        if st == ERR_CAPACITY:
+            cap_o, cap_m = no.value, nmem.value
+            continue
+        break
+    if st != OK:
+        raise RuntimeError(f"oracle rro_batch failed with status {st}")
+    return ops[: no.value].copy(), mem[: nmem.value].copy()

@@ -1,0 +1,37 @@
+"""The oracle against hand-worked instances (tests/golden/*.json).
+
+Each fixture was solved by hand from the rules of Alg. 1 / Sec. III.A-C and
+Alg. 2 / Sec. IV, with the derivation written in the file."""
+import glob
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.checks import grid_from_rows, replay_moves, assert_target_full, replay_ops
+
+GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.json")))
+
+
+@pytest.mark.parametrize("path", GOLDEN, ids=[os.path.basename(p)[:-5] for p in GOLDEN])
+def test_golden(path):
+    fx = json.load(open(path))
+    grid = grid_from_rows(fx["grid"])
+    rect = tuple(fx["rect"])
+    p = oracle.plan(grid, rect, with_trace=True)
+    assert p.status == fx["status"]
+    assert p.moves.tolist() == fx["moves"]
+    assert p.events.tolist() == fx["events"]
+    ops, mem = oracle.batch(p.moves, *grid.shape)
+    assert ops.tolist() == fx["ops"]
+    assert mem.tolist() == fx["members"]
+    if p.status == 0:
+        final = replay_moves(grid, rect, p.moves)
+        assert_target_full(final, rect, grid)
+        assert (replay_ops(grid, p.moves, ops, mem) == final).all()
+
+
+def test_golden_fixture_count():
+    assert len(GOLDEN) >= 5

@@ -1,0 +1,309 @@
+"""Pins of the oracle to facts outside itself (CPU only).
+
+P1 replay legality (Sec. II.B-C), P2 optimality of the 1D solves against a
+library assignment solver and exhaustive search (Sec. III.A), P4 the 2n-chain
+closed form (Sec. III.A, Complexity), P5 special cases, P6 feasibility
+(Sec. III.C), P7 iteration bounds (Sec. III.C Complexity, Alg. 2), pairing
+choices against exhaustive pair enumeration (Sec. III.C), and the geometry
+invariants of the generated path system (Sec. III.A, III.C).
+"""
+import itertools
+
+import numpy as np
+import pytest
+from scipy.optimize import linear_sum_assignment
+
+import gridgen
+import oracle
+from tests.checks import replay_moves, assert_target_full, path_len
+
+RNG = np.random.default_rng(20250408)
+
+
+def random_instance(rng, m, n, p, full_width=False):
+    grid = (rng.random((m, n)) < p).astype(np.uint8)
+    h = int(rng.integers(1, m + 1))
+    r0 = int(rng.integers(0, m - h + 1))
+    if full_width:
+        c0, c1 = 0, n
+    else:
+        w = int(rng.integers(1, n + 1))
+        c0 = int(rng.integers(0, n - w + 1))
+        c1 = c0 + w
+    return grid, (r0, c0, r0 + h, c1)
+
+
+def lsa_cost(src, dst):
+    if len(dst) == 0:
+        return 0
+    C = np.abs(np.subtract.outer(np.asarray(src), np.asarray(dst)))
+    r, c = linear_sum_assignment(C)
+    return int(C[r, c].sum())
+
+
+# ------------------------------------------------------------------ P1 / P6
+
+@pytest.mark.parametrize("full_width", [False, True])
+def test_replay_legal_random_small(full_width):
+    """P1 + P6: on random small grids a plan exists iff the total surplus is
+    non-negative, and every plan replays without collision and fills T."""
+    n_ok = n_inf = 0
+    for trial in range(1500):
+        m = int(RNG.integers(1, 11))
+        n = int(RNG.integers(1, 11))
+        p = float(RNG.uniform(0.2, 0.95))
+        grid, rect = random_instance(RNG, m, n, p, full_width)
+        res = oracle.plan(grid, rect, with_trace=True)
+        r0, c0, r1, c1 = rect
+        h, R = r1 - r0, m - (r1 - r0)
+        # total surplus: target columns K - h; other columns the atoms that can
+        # reach their reservoir rows (all reservoir cells if enough atoms)
+        tot = 0
+        for c in range(n):
+            K = int(grid[:, c].sum())
+            if c0 <= c < c1:
+                tot += K - h
+            else:
+                tot += R if K >= R else int(grid[:r0, c].sum() + grid[r1:, c].sum())
+        assert (res.status == 0) == (tot >= 0), (trial, rect)
+        if res.status == 0:
+            n_ok += 1
+            final = replay_moves(grid, rect, res.moves)
+            assert_target_full(final, rect, grid)
+            assert len(res.events) <= n                       # P7: loop bound
+        else:
+            n_inf += 1
+            assert len(res.moves) == 0
+    assert n_ok > 300 and n_inf > 50
+
+
+def test_replay_legal_generated_workloads():
+    """P1 on the seeded synthetic workloads at small and medium sizes."""
+    cases = [gridgen.square_instance(s, 0, 32, 0.6, 20) for s in range(8)]
+    cases += [gridgen.square_instance(s, 1, 96, 0.62) for s in range(3)]
+    cases += gridgen.mixed_instances(3, 6, sides=(32, 48, 64, 80), p_lo=0.5, p_hi=0.7)
+    for inst in cases:
+        res = oracle.plan(inst.grid, inst.rect)
+        if res.status == 0:
+            final = replay_moves(inst.grid, inst.rect, res.moves)
+            assert_target_full(final, inst.rect, inst.grid)
+
+
+def test_each_token_moves_at_most_once_in_paper_geometry():
+    """Sec. III.C/D: with delayed moves every token moves at most once. With
+    a full-width band (the paper's geometry) no move starts where an earlier
+    move ended."""
+    for trial in range(400):
+        m, n = int(RNG.integers(3, 12)), int(RNG.integers(2, 12))
+        grid, rect = random_instance(RNG, m, n, float(RNG.uniform(0.4, 0.9)), full_width=True)
+        res = oracle.plan(grid, rect)
+        if res.status != 0:
+            continue
+        arrived = set()
+        for mv in res.moves:
+            assert (int(mv[0]), int(mv[1])) not in arrived
+            arrived.add((int(mv[2]), int(mv[3])))
+
+
+# ------------------------------------------------------------------------ P2
+
+def test_window_is_optimal_vs_assignment_solver():
+    """P2: the contiguous-window 1D solve reaches the minimum-weight
+    T-saturating matching found by a general assignment solver, on every
+    random column of height <= 16."""
+    for trial in range(3000):
+        m = int(RNG.integers(1, 17))
+        h = int(RNG.integers(1, m + 1))
+        r0 = int(RNG.integers(0, m - h + 1))
+        K = int(RNG.integers(h, m + 1))
+        s = np.sort(RNG.choice(m, size=K, replace=False)).astype(np.int32)
+        w = oracle.window(s, r0, h)
+        cost = int(np.abs(s[w:w + h] - (r0 + np.arange(h))).sum())
+        assert cost == lsa_cost(s, r0 + np.arange(h)), (s, r0, h, w)
+        # smallest start among optimal windows
+        for w2 in range(w):
+            assert int(np.abs(s[w2:w2 + h] - (r0 + np.arange(h))).sum()) > cost
+
+
+def test_window_exhaustive_subsets():
+    """P2 by exhaustion: no choice of h sources, matched in any order, beats
+    the window (columns of height <= 10)."""
+    for trial in range(400):
+        m = int(RNG.integers(1, 11))
+        h = int(RNG.integers(1, m + 1))
+        r0 = int(RNG.integers(0, m - h + 1))
+        K = int(RNG.integers(h, m + 1))
+        s = np.sort(RNG.choice(m, size=K, replace=False)).astype(np.int32)
+        w = oracle.window(s, r0, h)
+        cost = int(np.abs(s[w:w + h] - (r0 + np.arange(h))).sum())
+        t = list(range(r0, r0 + h))
+        best = min(min(sum(abs(a - b) for a, b in zip(sub, perm)) for perm in itertools.permutations(t))
+                   for sub in itertools.combinations(s.tolist(), h)) if h <= 5 else None
+        if best is not None:
+            assert cost == best
+
+
+def test_split_optimal_over_all_subsets():
+    """P2 for the redistribution instance (Sec. III.C): choosing the a nearest
+    pool atoms above and x-a nearest below is as good as the best of all
+    x-subsets of the pool, each matched optimally."""
+    for trial in range(1500):
+        m = int(RNG.integers(3, 15))
+        h = int(RNG.integers(1, m - 1))
+        r0 = int(RNG.integers(1, m - h + 1)) if m - h >= 1 else 0
+        r1 = r0 + h
+        res_rows = [r for r in range(m) if r < r0 or r >= r1]
+        band = list(range(r0, r1))
+        nm = int(RNG.integers(0, h + 1))
+        # mandatory rows: a multiset (several tokens may project onto one row)
+        mand = RNG.choice(band + res_rows, size=nm, replace=True).astype(np.int32)
+        x = h - nm
+        pool = RNG.choice(res_rows, size=min(len(res_rows), x + int(RNG.integers(0, 4))), replace=False)
+        if len(pool) < x:
+            continue
+        top = pool[pool < r0].astype(np.int32)
+        bot = pool[pool >= r1].astype(np.int32)
+        a, cost = oracle.split(mand, top, bot, x, r0, h)
+        assert a >= 0
+        tgt = np.arange(r0, r1)
+        best = min(lsa_cost(np.concatenate([mand, np.array(sub, dtype=np.int32)]), tgt)
+                   for sub in itertools.combinations(pool.tolist(), x))
+        assert cost == best, (mand, top, bot, x, r0, h)
+
+
+def test_plan_columns_optimal():
+    """P2 inside full plans: every column's vertical displacement equals the
+    optimum assignment of the sources it uses to its targets (column phase:
+    its own atoms to the band or, outside the target columns, to its
+    reservoir cells)."""
+    for trial in range(300):
+        m, n = int(RNG.integers(2, 13)), int(RNG.integers(1, 9))
+        grid, rect = random_instance(RNG, m, n, float(RNG.uniform(0.3, 0.9)))
+        res = oracle.plan(grid, rect, with_trace=True)
+        if res.status != 0:
+            continue
+        r0, c0, r1, c1 = rect
+        h = r1 - r0
+        receivers = set(int(e[2]) for e in res.events)
+        for c in range(n):
+            atoms = np.nonzero(grid[:, c])[0]
+            if c in receivers:
+                continue
+            if c0 <= c < c1:
+                tgt = np.arange(r0, r1)
+            elif len(atoms) >= m - h:
+                tgt = np.array([r for r in range(m) if r < r0 or r >= r1])
+            else:
+                tgt = np.array([], dtype=int)
+            col_moves = res.moves[(res.moves[:, 1] == c) & (res.moves[:, 3] == c)]
+            used = np.abs(col_moves[:, 0] - col_moves[:, 2]).sum() if len(col_moves) else 0
+            assert int(used) == lsa_cost(atoms, tgt) if len(tgt) else int(used) == 0
+
+
+# ------------------------------------------------------------------------ P4
+
+@pytest.mark.parametrize("k", [1, 2, 5, 17, 64])
+def test_chain_closed_form(k):
+    """P4: 2k-chain with atoms on the first k traps and targets on the last k
+    needs k moves and k^2 elementary steps (Sec. III.A, Complexity)."""
+    grid = np.zeros((2 * k, 1), dtype=np.uint8)
+    grid[:k, 0] = 1
+    res = oracle.plan(grid, (k, 0, 2 * k, 1))
+    assert res.status == 0
+    assert len(res.moves) == k
+    assert path_len(res.moves) == k * k
+    ops, mem = oracle.batch(res.moves, 2 * k, 1)
+    assert len(ops) == k * k and len(mem) == k * k      # the paths chain: one token per batch
+
+
+# ------------------------------------------------------------------------ P5
+
+def test_special_cases():
+    # already solved: atoms exactly on the target, nothing else
+    g = np.zeros((6, 5), dtype=np.uint8)
+    g[1:4, 1:4] = 1
+    res = oracle.plan(g, (1, 1, 4, 4), with_trace=True)
+    assert res.status == 0 and len(res.moves) == 0 and len(res.events) == 0
+    # every column self-sufficient: no pairing, only vertical moves
+    for trial in range(200):
+        m, n = int(RNG.integers(4, 14)), int(RNG.integers(1, 9))
+        h = int(RNG.integers(1, m // 2 + 1))
+        g = np.zeros((m, n), dtype=np.uint8)
+        for c in range(n):
+            g[RNG.choice(m, size=int(RNG.integers(h, m + 1)), replace=False), c] = 1
+        r0 = int(RNG.integers(0, m - h + 1))
+        res = oracle.plan(g, (r0, 0, r0 + h, n), with_trace=True)
+        assert res.status == 0 and len(res.events) == 0
+        assert (res.moves[:, 1] == res.moves[:, 3]).all()
+    # single target column is the exact 1D solve of that column
+    g = np.zeros((9, 1), dtype=np.uint8)
+    g[[0, 2, 3, 7, 8], 0] = 1
+    res = oracle.plan(g, (3, 0, 6, 1))
+    assert path_len(res.moves) == lsa_cost(np.array([0, 2, 3, 7, 8]), np.arange(3, 6))
+    # no atoms at all
+    res = oracle.plan(np.zeros((4, 4), dtype=np.uint8), (1, 1, 3, 3))
+    assert res.status == 1 and len(res.moves) == 0
+
+
+def test_full_grid_target_no_reservoir():
+    """h = m (no reservoir): feasible iff every target column is full."""
+    g = np.ones((5, 4), dtype=np.uint8)
+    res = oracle.plan(g, (0, 1, 5, 3))
+    assert res.status == 0 and len(res.moves) == 0
+    g[2, 2] = 0
+    res = oracle.plan(g, (0, 1, 5, 3))
+    assert res.status == 1
+
+
+# ---------------------------------------------------------- pairing (Sec III.C)
+
+def test_pairing_choices_exhaustive():
+    """Every pairing iteration picks, among ALL donor/receiver pairs whose
+    in-between columns are at zero surplus (enumerated over every pair of
+    columns), the one maximising the exchanged tokens, then minimising the
+    gap, then the receiver's deficit (ties: receiver, then donor index); the
+    case follows from the two surpluses."""
+    checked = 0
+    for trial in range(1500):
+        m, n = int(RNG.integers(3, 13)), int(RNG.integers(2, 17))
+        grid, rect = random_instance(RNG, m, n, float(RNG.uniform(0.4, 0.8)), full_width=trial % 2 == 0)
+        res = oracle.plan(grid, rect, with_trace=True)
+        if res.status != 0:
+            continue
+        sig = res.sigma.astype(int).copy()
+        for (kase, i, j, x, a) in res.events:
+            best = None
+            for u in range(n):
+                for v in range(n):
+                    if sig[u] > 0 and sig[v] < 0:
+                        lo, hi = min(u, v), max(u, v)
+                        if all(sig[t] == 0 for t in range(lo + 1, hi)):
+                            key = (-min(sig[u], -sig[v]), hi - lo, -sig[v], v, u)
+                            best = key if best is None or key < best else best
+            assert best is not None
+            assert (best[4], best[3]) == (i, j)
+            assert x == min(sig[i], -sig[j])
+            want = 1 if sig[i] > -sig[j] else (2 if sig[i] == -sig[j] else 3)
+            assert kase == want
+            sig[i] -= x
+            sig[j] += x
+            checked += 1
+        assert (sig >= 0).all()
+    assert checked > 500
+
+
+def test_outer_columns_only_vertical_in_column_phase():
+    """Geometry invariants of the path system: column-phase moves stay in
+    their column; every L-shaped move starts in a reservoir row and ends in
+    the target band of a target column."""
+    for trial in range(300):
+        m, n = int(RNG.integers(3, 13)), int(RNG.integers(2, 13))
+        grid, rect = random_instance(RNG, m, n, float(RNG.uniform(0.4, 0.9)))
+        res = oracle.plan(grid, rect)
+        if res.status != 0:
+            continue
+        r0, c0, r1, c1 = rect
+        L = res.moves[res.moves[:, 1] != res.moves[:, 3]]
+        assert ((L[:, 0] < r0) | (L[:, 0] >= r1)).all()
+        assert ((L[:, 2] >= r0) & (L[:, 2] < r1)).all()
+        assert ((L[:, 3] >= c0) & (L[:, 3] < c1)).all()
