@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the red-rec planning + batching path on one GB300.
+
+Workload (one step): 4096 independent square grids, side uniform over
+{32, 48, ..., 256}, fill p uniform in [0.5, 0.7], centred target of side
+floor(0.7 * side), bit-packed uint32 rows; the whole batch is planned
+(Alg. 1) and batched (Alg. 2) by one rr_plan_batched(RR_WITH_BATCH) call.
+Inputs are seeded synthetic grids (gridgen), resident in HBM before timing.
+
+`--impl reference` times the CPU oracle instead (bounded samples of the same
+workload on the host cores). Under torchrun every rank plans its own 4096
+grids (weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gridgen  # noqa: E402
+
+METRIC = "red-rec grids/s and p50/p99 plan latency, batched/served vs plain; %HBM roof"
+WORKLOAD = "4096 square grids, side U{32..256 step 16}, p U[0.5,0.7], centred floor(0.7*side) target, bits32"
+KERNELS_PER_STEP = 15
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ oracle
+
+def oracle_sample(insts, budget_s, threads):
+    """Plan + batch grids in order with the CPU oracle on `threads` host
+    threads until the time budget is spent. Returns (grids done, seconds)."""
+    import oracle
+    oracle.build()
+
+    def one(inst):
+        p = oracle.plan(inst.grid, inst.rect)
+        if p.status == 0:
+            oracle.batch(p.moves, *inst.grid.shape)
+        return 1
+
+    t0 = time.perf_counter()
+    done = 0
+    it = iter(insts)
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        pending = set()
+        for _ in range(threads):
+            x = next(it, None)
+            if x is not None:
+                pending.add(ex.submit(one, x))
+        while pending:
+            fin, pending = cf.wait(pending, return_when=cf.FIRST_COMPLETED)
+            done += len(fin)
+            if time.perf_counter() - t0 < budget_s:
+                for _ in fin:
+                    x = next(it, None)
+                    if x is not None:
+                        pending.add(ex.submit(one, x))
+    return done, time.perf_counter() - t0
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.lines = []
+
+    def start(self, gpu_index):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ ours
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2504_06182_gb300 as rr
+    from paper_2504_06182_gb300.planner import Planner, pack_instances, unpack_instances
+
+    insts = gridgen.mixed_instances(args.seed + 1000 * rank, args.count)
+    # CPU oracle baseline on host cores before any GPU work (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        done, secs = oracle_sample(insts, args.cpu_budget, threads)
+        cpu = {"value": done / secs, "unit": "grids/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {done} grids of the workload (plan + batching), {threads} host threads, "
+                         f"{secs:.1f} s"}
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+
+    # packed grids: one pinned host buffer, one device buffer
+    words = [gridgen.pack_bits32(i.grid).view(np.int32).ravel() for i in insts]
+    offs = np.cumsum([0] + [len(w) for w in words])
+    host = torch.empty(int(offs[-1]), dtype=torch.int32).pin_memory()
+    host.numpy()[:] = np.concatenate(words)
+    grids = host.to(dev)
+    count = len(insts)
+    sides = [i.grid.shape[0] for i in insts]
+    max_side = max(sides)
+
+    P = Planner(arena_bytes=int(os.environ.get("RR_ARENA_GB", "24")) << 30)
+
+    def entries(moves=None, ops=None, mem=None, caps=None):
+        out = []
+        for g, inst in enumerate(insts):
+            s = sides[g]
+            e = dict(grid=grids[offs[g]:offs[g + 1]], layout=rr.RR_BITS32, m=s, n=s, rect=inst.rect)
+            if caps is not None:
+                cm, co, cs, om, oo, os_ = caps[g]
+                e.update(moves=moves[om:om + 1] if cm else None, cap_moves=cm,
+                         ops=ops[oo:oo + 1] if co else None, cap_ops=co,
+                         members=mem[os_:os_ + 1] if cs else None, cap_members=cs)
+            out.append(e)
+        return out
+
+    # sizing: plan with no output room gives the move counts
+    d_inst = pack_instances(entries())
+    rr.rr_plan_batched(P.ctx, d_inst, count, max_side, 0)
+    torch.cuda.synchronize()
+    r = unpack_instances(d_inst, count)
+    n_moves = np.array([x.n_moves for x in r], dtype=np.int64)
+    moves = torch.empty((int(n_moves.sum()) + 1, 4), dtype=torch.int32, device=dev)
+    mo = np.concatenate([[0], np.cumsum(n_moves)])
+    caps = [(int(n_moves[g]), 0, 0, int(mo[g]), 0, 0) for g in range(count)]
+    d_inst = pack_instances(entries(moves, None, None, caps))
+    rr.rr_plan_batched(P.ctx, d_inst, count, max_side, rr.RR_WITH_BATCH)
+    torch.cuda.synchronize()
+    r = unpack_instances(d_inst, count)
+    n_steps = np.array([x.n_steps for x in r], dtype=np.int64)
+    so = np.concatenate([[0], np.cumsum(n_steps)])
+    ops = torch.empty((int(n_steps.sum()) + 1, 3), dtype=torch.int32, device=dev)
+    mem = torch.empty((int(n_steps.sum()) + 1,), dtype=torch.int32, device=dev)
+    caps = [(int(n_moves[g]), int(n_steps[g]), int(n_steps[g]), int(mo[g]), int(so[g]), int(so[g]))
+            for g in range(count)]
+    d_inst = pack_instances(entries(moves, ops, mem, caps))
+    inst_host = d_inst.cpu().pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    stream = torch.cuda.current_stream()
+
+    def step():
+        st = rr.rr_plan_batched(P.ctx, d_inst, count, max_side, rr.RR_WITH_BATCH, stream)
+        if st != rr.RR_OK:
+            raise rr.RRError(st, rr.rr_last_error(P.ctx))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    res = unpack_instances(d_inst, count)
+    bad = [(g, x.status) for g, x in enumerate(res) if x.status not in (rr.RR_OK, rr.RR_INFEASIBLE)]
+    if bad:
+        raise RuntimeError(f"instances failed: {bad[:5]}")
+
+    rr.rr_set_tracing(P.ctx, True)
+    stage_tot = {}
+    times = []
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        for nm, ms in rr.rr_stage_times(P.ctx):
+            stage_tot[nm] = stage_tot.get(nm, 0.0) + ms
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    rr.rr_set_tracing(P.ctx, False)
+    elapsed_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    res = unpack_instances(d_inst, count)
+    tot_moves = sum(x.n_moves for x in res)
+    tot_ops = sum(x.n_ops for x in res)
+    tot_mem = sum(x.n_members for x in res)
+    feasible = sum(x.status == rr.RR_OK for x in res)
+
+    # end to end through the public call with host buffers: H2D of the packed
+    # grids and descriptors, the planning call, D2H of the per-grid results
+    e2e_ms = []
+    h2d = host.numel() * 4 + inst_host.numel()
+    d2h = inst_host.numel()
+    back = torch.empty_like(inst_host).pin_memory()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        grids.copy_(host, non_blocking=True)
+        d_inst.copy_(inst_host, non_blocking=True)
+        step()
+        back.copy_(d_inst, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_total = float(sum(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    # dominant kernel and its algorithmic bytes per launch
+    dom = max(stage_tot, key=stage_tot.get) if stage_tot else None
+    grid_bytes = host.numel() * 4
+    alg = {
+        "k_sim": 16 * tot_moves + 12 * tot_ops + 4 * tot_mem,
+        "k_bsort": 8 * (tot_mem + tot_moves),
+        "k_emit_recv": 16 * tot_moves,
+        "k_transpose": 2 * grid_bytes,
+    }
+    roof = None
+    if dom is not None:
+        avg_ms = stage_tot[dom] / args.steps
+        byt = alg.get(dom)
+        if byt is not None:
+            ach = byt / (avg_ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak_gbs, "unit": "GB/s",
+                    "frac": ach / peak_gbs, "traffic": None, "peak_source": "measured" if peaks else "fallback",
+                    "alg_bytes_per_launch": int(byt), "avg_ms": avg_ms}
+    value = count * world * args.steps / (elapsed_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "grids/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grids_per_gpu": count, "layout": "bits32", "seed": args.seed,
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world}"},
+        "e2e": {"value": count * world * args.steps / (e2e_total * 1e-3), "unit": "grids/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_tot.items(), key=lambda kv: -kv[1])},
+        "totals_per_step": {"moves": int(tot_moves), "ops": int(tot_ops), "steps": int(tot_mem),
+                            "feasible": int(feasible), "grids": count},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    insts = gridgen.mixed_instances(args.seed, args.count)
+    threads = os.cpu_count() or 1
+    budget = float(os.environ.get("RR_REF_STEP_S", "8"))
+    for _ in range(args.warmup):
+        oracle_sample(insts[:threads], budget / 4, threads)
+    done_tot, secs_tot = 0, 0.0
+    for s in range(args.steps):
+        # each step a bounded sample: consecutive grids from a rotating start
+        start = (s * 97) % max(1, len(insts) - 1)
+        done, secs = oracle_sample(insts[start:] + insts[:start], budget, threads)
+        done_tot += done
+        secs_tot += secs
+    value = done_tot / secs_tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "grids/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs_tot * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grids_per_gpu": args.count, "layout": "bits32", "seed": args.seed},
+        "cpu_baseline": {"value": value, "unit": "grids/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{done_tot} grids over {args.steps} steps of ~{budget:.0f} s, "
+                                   f"{threads} host threads"},
+        "e2e": {"value": value, "unit": "grids/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,129 @@
+/*
+ * rr.h -- C ABI of the GB300 red-rec planner and batching routine.
+ *
+ * Method: Afiouni et al., "Efficient algorithms to solve atom reconfiguration
+ * problems III" (arXiv 2504.06182): the improved red-rec algorithm (Alg. 1,
+ * Sec. III.C, executed in the column order of the parallel variant of Sec.
+ * III.D) and the batching routine (Alg. 2 with the local constraint set of
+ * Sec. IV). All arithmetic is integer.
+ *
+ * Memory: every buffer argument named d_* is caller-owned DEVICE memory; the
+ * library never frees or retains it. Host pointers (n_moves, n_ops, ...) are
+ * written before the call returns. Workspace lives in the context.
+ * Streams: work is issued on `stream`; calls that return counts to host
+ * pointers synchronise that stream before returning.
+ * Errors: every entry point returns an rr_status; no CPU fallback exists and
+ * nothing fails silently. On RR_ERR_CAPACITY the required sizes are written to
+ * the count pointers and no output element is valid.
+ * Limits: 1 <= m, n <= RR_MAX_SIDE.
+ */
+#ifndef RR_H
+#define RR_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RR_MAX_SIDE 1024
+
+typedef enum {
+    RR_OK = 0,
+    RR_INFEASIBLE = 1,       /* total surplus negative: no plan, zero moves (Sec. III.C) */
+    RR_ERR_ARG = -1,         /* bad argument (sizes, rectangle, null pointers, layout) */
+    RR_ERR_CAPACITY = -2,    /* an output buffer is too small; required sizes returned */
+    RR_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    RR_ERR_TIMEOUT = -4,     /* a bounded device loop hit its iteration limit */
+    RR_ERR_WORKSPACE = -5,   /* the context's device arena is too small */
+    RR_ERR_INTERNAL = -6     /* a device-side invariant check failed */
+} rr_status;
+
+typedef enum { RR_U8 = 0, RR_BITS32 = 1 } rr_layout;
+
+/* Target rectangle: rows [r0, r1), columns [c0, c1), half-open,
+ * 0 <= r0 < r1 <= m, 0 <= c0 < c1 <= n. */
+typedef struct { int32_t r0, c0, r1, c1; } rr_rect;
+
+/* One move = one extraction-displacement-implantation cycle along a shortest
+ * path (Sec. II.A-C): along row src_row from src_col to dst_col, then along
+ * column dst_col from src_row to dst_row. */
+typedef struct { int32_t src_row, src_col, dst_row, dst_col; } rr_move;
+
+/* One batch of Alg. 2: members[first .. first+count) are the ids (indices into
+ * the move list) of the moves whose tokens advance one elementary step in
+ * direction dir: 0 = row-1, 1 = row+1, 2 = column-1, 3 = column+1. */
+typedef struct { int32_t dir, first, count; } rr_op;
+
+typedef struct rr_ctx rr_ctx;
+
+/* Context: owns the device workspace arena (bytes; 0 = default 1 GiB) on the
+ * current CUDA device. Not thread-safe: one host thread per context. */
+int rr_ctx_create(rr_ctx **ctx, int64_t arena_bytes);
+int rr_ctx_destroy(rr_ctx *ctx);
+
+/* Plan one grid (Alg. 1). Grid layout: RR_U8 = m*n bytes row-major, 0/1;
+ * RR_BITS32 = m rows of ceil(n/32) uint32 words, bit (c & 31) of word (c >> 5)
+ * is trap c, least significant bit first. Moves are emitted in execution
+ * order: column-phase units in column order, then receiver units in the order
+ * the receivers become saturated; inside a unit, paths toward larger rows by
+ * descending target row, then paths toward smaller rows by ascending target
+ * row (Sec. III.A). cap = capacity of d_moves in moves. Writes *n_moves
+ * (required count on RR_ERR_CAPACITY; 0 on RR_INFEASIBLE). Synchronises. */
+int rr_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect,
+            rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream);
+
+/* Batch a move list (Alg. 2 + Sec. IV): dependencies = every earlier move
+ * whose path shares a vertex; ready moves are visited in ascending id and a
+ * move's next step joins the batch iff it has the first member's direction and
+ * its token shares a row or a column with every member's token. d_moves must
+ * be an unobstructed ordered path system on an m x n grid (e.g. rr_plan's
+ * output). Writes *n_ops and *n_members (= total elementary steps).
+ * Synchronises. */
+int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, int m, int n,
+             rr_op *d_ops, int64_t cap_ops, int32_t *d_members, int64_t cap_members,
+             int64_t *n_ops, int64_t *n_members, cudaStream_t stream);
+
+/* Many independent grids in one launch sequence (device-resident
+ * descriptors). Inputs per instance: grid, layout, m, n, rect, output
+ * pointers and capacities. Outputs per instance: status, n_moves, n_steps
+ * (total elementary steps), and with RR_WITH_BATCH n_ops and n_members.
+ * On RR_ERR_CAPACITY for an instance, its counts hold the required sizes
+ * (n_ops is then an upper bound, = n_steps). The call itself returns RR_OK
+ * when it issued the work (no synchronisation); read the per-instance status
+ * after synchronising the stream. */
+#define RR_WITH_BATCH 1
+typedef struct {
+    const void *grid;
+    int32_t layout, m, n, pad0;
+    rr_rect rect;
+    rr_move *moves;     int64_t cap_moves;
+    rr_op *ops;         int64_t cap_ops;
+    int32_t *members;   int64_t cap_members;
+    int64_t n_moves, n_steps, n_ops, n_members;   /* outputs */
+    int32_t status, pad1;                         /* output */
+} rr_instance;
+
+/* count in [1, 65535]; max_side bounds m and n of every instance (an
+ * instance above it gets RR_ERR_ARG); it sizes the launch shapes. The call
+ * may grow the context's descriptor table (a synchronous cudaMalloc), so the
+ * first call with a larger count must not be inside stream capture. */
+int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
+                    cudaStream_t stream);
+
+/* Stage tracing. With tracing on, every public call records a CUDA event on
+ * its stream before each kernel and after the last one. rr_stage_times then
+ * waits for those events and writes, for the most recent call, each kernel's
+ * name (static strings) and elapsed milliseconds; it returns the number of
+ * stages written (at most cap) or a negative rr_status. */
+int rr_set_tracing(rr_ctx *ctx, int enable);
+int rr_stage_times(rr_ctx *ctx, float *ms, const char **names, int cap);
+
+/* Last error text of this context (static storage, never NULL). */
+const char *rr_last_error(rr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

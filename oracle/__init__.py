@@ -47,6 +47,8 @@ def lib():
         L.rro_plan.restype = i32
         L.rro_batch.argtypes = [P, i64, i32, i32, P, i64, P, i64, P, P]
         L.rro_batch.restype = i32
+        L.rro_batch_prefix.argtypes = [P, i64, i32, i32, i64, P, i64, P, i64, P, P]
+        L.rro_batch_prefix.restype = i32
         _lib = L
     return _lib
 
@@ -104,8 +106,9 @@ def plan(grid: np.ndarray, rect, with_trace: bool = False) -> Plan:
                 events[: ne.value].copy() if with_trace else None)
 
 
-def batch(moves: np.ndarray, m: int, n: int):
-    """Returns (ops (b, 3) int32: dir, first, count; members (s,) int32)."""
+def batch(moves: np.ndarray, m: int, n: int, max_ops: int | None = None):
+    """Returns (ops (b, 3) int32: dir, first, count; members (s,) int32).
+    With max_ops, only the first max_ops batches."""
     moves = np.ascontiguousarray(moves, dtype=np.int32).reshape(-1, 4)
     no = ctypes.c_int64(0)
     nmem = ctypes.c_int64(0)
@@ -113,8 +116,12 @@ def batch(moves: np.ndarray, m: int, n: int):
     while True:
         ops = np.zeros((max(cap_o, 1), 3), dtype=np.int32)
         mem = np.zeros(max(cap_m, 1), dtype=np.int32)
-        st = lib().rro_batch(_ptr(moves), len(moves), m, n, _ptr(ops), cap_o, _ptr(mem), cap_m,
-                             ctypes.byref(no), ctypes.byref(nmem))
+        if max_ops is None:
+            st = lib().rro_batch(_ptr(moves), len(moves), m, n, _ptr(ops), cap_o, _ptr(mem), cap_m,
+                                 ctypes.byref(no), ctypes.byref(nmem))
+        else:
+            st = lib().rro_batch_prefix(_ptr(moves), len(moves), m, n, int(max_ops), _ptr(ops), cap_o,
+                                        _ptr(mem), cap_m, ctypes.byref(no), ctypes.byref(nmem))
         if st == ERR_CAPACITY:
             cap_o, cap_m = no.value, nmem.value
             continue

@@ -423,9 +423,28 @@ static int path_dir(const mv_t *p, int t)
     return p->dr > p->sr ? 1 : 0;
 }
 
+static int batch_impl(const int32_t *moves_in, int64_t n_moves, int m, int n,
+                      int64_t max_ops, int32_t *ops, int64_t cap_ops, int32_t *members,
+                      int64_t cap_members, int64_t *n_ops, int64_t *n_members);
+
 int rro_batch(const int32_t *moves_in, int64_t n_moves, int m, int n,
               int32_t *ops, int64_t cap_ops, int32_t *members,
               int64_t cap_members, int64_t *n_ops, int64_t *n_members)
+{
+    return batch_impl(moves_in, n_moves, m, n, -1, ops, cap_ops, members, cap_members, n_ops, n_members);
+}
+
+int rro_batch_prefix(const int32_t *moves_in, int64_t n_moves, int m, int n, int64_t max_ops,
+                     int32_t *ops, int64_t cap_ops, int32_t *members,
+                     int64_t cap_members, int64_t *n_ops, int64_t *n_members)
+{
+    if (max_ops < 0) return E_ARG;
+    return batch_impl(moves_in, n_moves, m, n, max_ops, ops, cap_ops, members, cap_members, n_ops, n_members);
+}
+
+static int batch_impl(const int32_t *moves_in, int64_t n_moves, int m, int n,
+                      int64_t max_ops, int32_t *ops, int64_t cap_ops, int32_t *members,
+                      int64_t cap_members, int64_t *n_ops, int64_t *n_members)
 {
     if (!n_ops || !n_members || m < 1 || n < 1 || n_moves < 0 || (n_moves > 0 && !moves_in))
         return E_ARG;
@@ -484,7 +503,7 @@ int rro_batch(const int32_t *moves_in, int64_t n_moves, int m, int n,
         if (blocked[b] == 0) ready[nready++] = (int32_t)b;   /* ascending ids */
     }
 
-    while (unfinished > 0) {
+    while (unfinished > 0 && (max_ops < 0 || nop < max_ops)) {
         if (nready == 0) { st = E_BUG; goto done; }
         int64_t nq = nready, na = 0, nn = 0;
         memcpy(Q, ready, sizeof(int32_t) * (size_t)nq);

@@ -61,6 +61,13 @@ int rro_batch(const int32_t *moves, int64_t n_moves, int m, int n,
               int32_t *ops, int64_t cap_ops, int32_t *members,
               int64_t cap_members, int64_t *n_ops, int64_t *n_members);
 
+/* Same routine, stopped after the first max_ops batches (a leading sample of
+ * the batch list for inputs too large to batch completely). */
+int rro_batch_prefix(const int32_t *moves, int64_t n_moves, int m, int n,
+                     int64_t max_ops, int32_t *ops, int64_t cap_ops,
+                     int32_t *members, int64_t cap_members, int64_t *n_ops,
+                     int64_t *n_members);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,160 @@
+"""GB300 red-rec planner and batching routine (arXiv 2504.06182, Alg. 1 and
+Alg. 2) -- Python binding of the C ABI in include/rr.h.
+
+The functions below carry the C names and only marshal arguments: every step
+of the planning and batching path runs in the CUDA library librr.so. PyTorch
+is used for device memory and streams. If librr.so is missing the import of
+the binding fails loudly; nothing falls back to a CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librr.so")
+
+RR_OK, RR_INFEASIBLE = 0, 1
+RR_ERR_ARG, RR_ERR_CAPACITY, RR_ERR_CUDA = -1, -2, -3
+RR_ERR_TIMEOUT, RR_ERR_WORKSPACE, RR_ERR_INTERNAL = -4, -5, -6
+RR_U8, RR_BITS32 = 0, 1
+RR_WITH_BATCH = 1
+RR_MAX_SIDE = 1024
+STATUS_NAMES = {0: "OK", 1: "INFEASIBLE", -1: "ERR_ARG", -2: "ERR_CAPACITY", -3: "ERR_CUDA",
+                -4: "ERR_TIMEOUT", -5: "ERR_WORKSPACE", -6: "ERR_INTERNAL"}
+
+
+class rr_rect(ctypes.Structure):
+    _fields_ = [("r0", ctypes.c_int32), ("c0", ctypes.c_int32), ("r1", ctypes.c_int32), ("c1", ctypes.c_int32)]
+
+
+class rr_move(ctypes.Structure):
+    _fields_ = [("src_row", ctypes.c_int32), ("src_col", ctypes.c_int32),
+                ("dst_row", ctypes.c_int32), ("dst_col", ctypes.c_int32)]
+
+
+class rr_op(ctypes.Structure):
+    _fields_ = [("dir", ctypes.c_int32), ("first", ctypes.c_int32), ("count", ctypes.c_int32)]
+
+
+class rr_instance(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_void_p), ("layout", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("n", ctypes.c_int32), ("pad0", ctypes.c_int32), ("rect", rr_rect),
+                ("moves", ctypes.c_void_p), ("cap_moves", ctypes.c_int64),
+                ("ops", ctypes.c_void_p), ("cap_ops", ctypes.c_int64),
+                ("members", ctypes.c_void_p), ("cap_members", ctypes.c_int64),
+                ("n_moves", ctypes.c_int64), ("n_steps", ctypes.c_int64),
+                ("n_ops", ctypes.c_int64), ("n_members", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("pad1", ctypes.c_int32)]
+
+
+EXPORTS = ("rr_ctx_create", "rr_ctx_destroy", "rr_plan", "rr_batch", "rr_plan_batched", "rr_set_tracing",
+           "rr_stage_times", "rr_last_error")
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librr.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: build it with paper_2504_06182_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    L.rr_ctx_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), I64]
+    L.rr_ctx_create.restype = I32
+    L.rr_ctx_destroy.argtypes = [P]
+    L.rr_ctx_destroy.restype = I32
+    L.rr_plan.argtypes = [P, P, I32, I32, I32, rr_rect, P, I64, ctypes.POINTER(I64), P]
+    L.rr_plan.restype = I32
+    L.rr_batch.argtypes = [P, P, I64, I32, I32, P, I64, P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64), P]
+    L.rr_batch.restype = I32
+    L.rr_plan_batched.argtypes = [P, P, I32, I32, I32, P]
+    L.rr_plan_batched.restype = I32
+    L.rr_set_tracing.argtypes = [P, I32]
+    L.rr_set_tracing.restype = I32
+    L.rr_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p), I32]
+    L.rr_stage_times.restype = I32
+    L.rr_last_error.argtypes = [P]
+    L.rr_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _addr(x) -> int:
+    """Device address of a torch tensor, or an integer address as is."""
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    return int(x)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+class RRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+# ------------------------------------------------------------- C-ABI names
+
+def rr_ctx_create(arena_bytes: int = 0) -> int:
+    h = ctypes.c_void_p(0)
+    st = load().rr_ctx_create(ctypes.byref(h), int(arena_bytes))
+    if st != RR_OK:
+        raise RRError(st, load().rr_last_error(None).decode())
+    return h.value
+
+
+def rr_ctx_destroy(ctx: int) -> int:
+    return load().rr_ctx_destroy(ctx)
+
+
+def rr_last_error(ctx) -> str:
+    return load().rr_last_error(ctx).decode()
+
+
+def rr_plan(ctx, d_grid, layout, m, n, rect, d_moves, cap, stream=None):
+    """Returns (status, n_moves)."""
+    nm = ctypes.c_int64(0)
+    st = load().rr_plan(ctx, _addr(d_grid), int(layout), int(m), int(n), rr_rect(*[int(v) for v in rect]),
+                        _addr(d_moves), int(cap), ctypes.byref(nm), _stream(stream))
+    return st, nm.value
+
+
+def rr_batch(ctx, d_moves, n_moves, m, n, d_ops, cap_ops, d_members, cap_members, stream=None):
+    """Returns (status, n_ops, n_members)."""
+    no, nmem = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = load().rr_batch(ctx, _addr(d_moves), int(n_moves), int(m), int(n), _addr(d_ops), int(cap_ops),
+                         _addr(d_members), int(cap_members), ctypes.byref(no), ctypes.byref(nmem),
+                         _stream(stream))
+    return st, no.value, nmem.value
+
+
+def rr_plan_batched(ctx, d_inst, count, max_side, flags=0, stream=None) -> int:
+    return load().rr_plan_batched(ctx, _addr(d_inst), int(count), int(max_side), int(flags), _stream(stream))
+
+
+def rr_set_tracing(ctx, enable: bool) -> int:
+    return load().rr_set_tracing(ctx, 1 if enable else 0)
+
+
+def rr_stage_times(ctx, cap: int = 32):
+    """[(kernel name, ms)] of the most recent traced call."""
+    ms = (ctypes.c_float * cap)()
+    names = (ctypes.c_char_p * cap)()
+    k = load().rr_stage_times(ctx, ms, names, cap)
+    if k < 0:
+        raise RRError(k, rr_last_error(ctx))
+    return [(names[i].decode(), float(ms[i])) for i in range(k)]

@@ -1,0 +1,290 @@
+// rr_capi.cu -- the C ABI (include/rr.h): context, workspace arena and the
+// launch sequences of the planner (Alg. 1) and the batching routine (Alg. 2).
+#include <cstdio>
+#include <cstring>
+#include <cstdarg>
+#include <algorithm>
+#include "rr_internal.cuh"
+
+namespace rrk {
+__global__ void k_plan_setup(rr_instance *, JobWS *, int, int, Arena);
+__global__ void k_transpose(rr_instance *, JobWS *, int);
+__global__ void k_colstats(rr_instance *, JobWS *, int);
+__global__ void k_pair(rr_instance *, JobWS *, int);
+__global__ void k_emit_cols(rr_instance *, JobWS *, int);
+__global__ void k_emit_recv(rr_instance *, JobWS *, int);
+__global__ void k_bsetup(rr_instance *, JobWS *, int, Arena);
+__global__ void k_bcount(rr_instance *, JobWS *, int);
+__global__ void k_bscan_cells(rr_instance *, JobWS *, int);
+__global__ void k_bfill(rr_instance *, JobWS *, int);
+__global__ void k_bsort(rr_instance *, JobWS *, int);
+__global__ void k_bsucc_count(rr_instance *, JobWS *, int);
+__global__ void k_bsucc_scan(rr_instance *, JobWS *, int, Arena);
+__global__ void k_bsucc_fill(rr_instance *, JobWS *, int);
+__global__ void k_sim(rr_instance *, JobWS *, int);
+}  // namespace rrk
+
+using namespace rrk;
+
+static_assert(sizeof(rr_instance) == 128, "rr_instance layout is part of the ABI");
+
+struct rr_ctx {
+    int device;
+    char *arena;
+    unsigned long long arena_size;
+    unsigned long long *d_top;
+    rr_instance *d_one;       // descriptor slot of the single-grid entry points
+    JobWS *d_ws;
+    int ws_cap;
+    char err[256];
+    // stage tracing: events recorded on the launching stream around every kernel
+    int tracing;
+    int nmarks;
+    cudaEvent_t marks[32];
+    const char *names[32];
+};
+
+static void mark(rr_ctx *ctx, cudaStream_t s, const char *name)
+{
+    if (!ctx->tracing || ctx->nmarks >= 32) return;
+    if (!ctx->marks[ctx->nmarks]) cudaEventCreate(&ctx->marks[ctx->nmarks]);
+    cudaEventRecord(ctx->marks[ctx->nmarks], s);
+    ctx->names[ctx->nmarks] = name;
+    ++ctx->nmarks;
+}
+
+static char g_err[256] = "";
+
+static int fail(rr_ctx *ctx, int code, const char *fmt, ...)
+{
+    char *dst = ctx ? ctx->err : g_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return fail(ctx, RR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static int ensure_ws(rr_ctx *ctx, int count)
+{
+    if (count <= ctx->ws_cap) return RR_OK;
+    int cap = std::max(count, 2 * ctx->ws_cap);
+    if (ctx->d_ws) CUDA_TRY(cudaFree(ctx->d_ws));
+    ctx->d_ws = nullptr;
+    ctx->ws_cap = 0;
+    CUDA_TRY(cudaMalloc(&ctx->d_ws, sizeof(JobWS) * (size_t)cap));
+    ctx->ws_cap = cap;
+    return RR_OK;
+}
+
+extern "C" int rr_ctx_create(rr_ctx **out, int64_t arena_bytes)
+{
+    rr_ctx *ctx = nullptr;
+    if (!out) return fail(nullptr, RR_ERR_ARG, "rr_ctx_create: null output pointer");
+    *out = nullptr;
+    ctx = new (std::nothrow) rr_ctx();
+    if (!ctx) return fail(nullptr, RR_ERR_ARG, "rr_ctx_create: out of host memory");
+    std::memset(ctx, 0, sizeof(*ctx));
+    if (arena_bytes <= 0) arena_bytes = 1ll << 30;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->arena, (size_t)arena_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_top, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_one, sizeof(rr_instance));
+    if (e != cudaSuccess) {
+        fail(nullptr, RR_ERR_CUDA, "rr_ctx_create: %s", cudaGetErrorString(e));
+        if (ctx->arena) cudaFree(ctx->arena);
+        if (ctx->d_top) cudaFree(ctx->d_top);
+        if (ctx->d_one) cudaFree(ctx->d_one);
+        delete ctx;
+        return RR_ERR_CUDA;
+    }
+    ctx->arena_size = (unsigned long long)arena_bytes;
+    int st = ensure_ws(ctx, 1);
+    if (st != RR_OK) { rr_ctx_destroy(ctx); return st; }
+    *out = ctx;
+    return RR_OK;
+}
+
+extern "C" int rr_ctx_destroy(rr_ctx *ctx)
+{
+    if (!ctx) return RR_ERR_ARG;
+    cudaFree(ctx->arena);
+    cudaFree(ctx->d_top);
+    cudaFree(ctx->d_one);
+    cudaFree(ctx->d_ws);
+    for (int i = 0; i < 32; ++i) if (ctx->marks[i]) cudaEventDestroy(ctx->marks[i]);
+    delete ctx;
+    return RR_OK;
+}
+
+extern "C" const char *rr_last_error(rr_ctx *ctx) { return ctx ? ctx->err : g_err; }
+
+static Arena arena_of(rr_ctx *ctx)
+{
+    Arena A;
+    A.base = ctx->arena;
+    A.size = ctx->arena_size;
+    A.top = ctx->d_top;
+    return A;
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Planning kernels over `count` device descriptors whose sides are <= max_side.
+static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, cudaStream_t s)
+{
+    const Arena A = arena_of(ctx);
+    const int colBlocks = clampi(std::max(1, 4096 / count), 1, (max_side + 7) / 8);
+    const int tiles = ((max_side + 31) / 32) * ((max_side + 31) / 32);
+    const int trBlocks = clampi(std::max(1, 4096 / count), 1, (tiles + 7) / 8);
+    const int recvBlocks = clampi(std::max(1, 2048 / count), 1, max_side);
+    mark(ctx, s, "k_plan_setup");
+    k_plan_setup<<<(count + 127) / 128, 128, 0, s>>>(d_inst, ctx->d_ws, count, max_side, A);
+    mark(ctx, s, "k_transpose");
+    k_transpose<<<dim3(trBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    mark(ctx, s, "k_colstats");
+    k_colstats<<<dim3(colBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    const size_t pairSmem = (size_t)max_side * 30 + 64;
+    mark(ctx, s, "k_pair");
+    k_pair<<<count, 32, pairSmem, s>>>(d_inst, ctx->d_ws, count);
+    mark(ctx, s, "k_emit_cols");
+    k_emit_cols<<<dim3(colBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    mark(ctx, s, "k_emit_recv");
+    k_emit_recv<<<dim3(recvBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    mark(ctx, s, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    return RR_OK;
+}
+
+static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, cudaStream_t s)
+{
+    const Arena A = arena_of(ctx);
+    const int pathBlocks = clampi(std::max(1, 8192 / count), 1, 512);
+    const int cellBlocks = clampi(std::max(1, 8192 / count), 1, (max_side * max_side + 255) / 256);
+    mark(ctx, s, "k_bsetup");
+    k_bsetup<<<count, 512, 0, s>>>(d_inst, ctx->d_ws, count, A);
+    mark(ctx, s, "k_bcount");
+    k_bcount<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    mark(ctx, s, "k_bscan_cells");
+    k_bscan_cells<<<count, 1024, 0, s>>>(d_inst, ctx->d_ws, count);
+    mark(ctx, s, "k_bfill");
+    k_bfill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    mark(ctx, s, "k_bsort");
+    k_bsort<<<dim3(cellBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    mark(ctx, s, "k_bsucc_count");
+    k_bsucc_count<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    mark(ctx, s, "k_bsucc_scan");
+    k_bsucc_scan<<<count, 1024, 0, s>>>(d_inst, ctx->d_ws, count, A);
+    mark(ctx, s, "k_bsucc_fill");
+    k_bsucc_fill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    const int Wm = (max_side + 31) / 32;
+    const size_t simSmem = sizeof(int32_t) * (size_t)(8 * max_side + 4 * Wm + max_side + 2) + 64;
+    mark(ctx, s, "k_sim");
+    k_sim<<<count, 32, simSmem, s>>>(d_inst, ctx->d_ws, count);
+    mark(ctx, s, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    return RR_OK;
+}
+
+static bool rect_ok(int m, int n, rr_rect R)
+{
+    return m >= 1 && n >= 1 && m <= RR_MAX_SIDE && n <= RR_MAX_SIDE && R.r0 >= 0 && R.r0 < R.r1 &&
+           R.r1 <= m && R.c0 >= 0 && R.c0 < R.c1 && R.c1 <= n;
+}
+
+extern "C" int rr_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect,
+                       rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream)
+{
+    if (!ctx || !d_grid || !n_moves || (layout != RR_U8 && layout != RR_BITS32) || !rect_ok(m, n, rect) ||
+        cap < 0 || (cap > 0 && !d_moves))
+        return fail(ctx, RR_ERR_ARG, "rr_plan: bad argument (m=%d n=%d rect=[%d,%d,%d,%d] layout=%d cap=%lld)", m, n,
+                    rect.r0, rect.c0, rect.r1, rect.c1, layout, (long long)cap);
+    rr_instance h;
+    std::memset(&h, 0, sizeof(h));
+    h.grid = d_grid; h.layout = layout; h.m = m; h.n = n; h.rect = rect;
+    h.moves = d_moves; h.cap_moves = cap;
+    ctx->nmarks = 0;
+    CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_one, &h, sizeof(h), cudaMemcpyHostToDevice, stream));
+    int st = launch_plan(ctx, ctx->d_one, 1, std::max(m, n), stream);
+    if (st != RR_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(&h, ctx->d_one, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    *n_moves = h.n_moves;
+    if (h.status < 0) return fail(ctx, h.status, "rr_plan: device status %d (n_moves=%lld)", h.status, (long long)h.n_moves);
+    return h.status;
+}
+
+extern "C" int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, int m, int n, rr_op *d_ops,
+                        int64_t cap_ops, int32_t *d_members, int64_t cap_members, int64_t *n_ops,
+                        int64_t *n_members, cudaStream_t stream)
+{
+    if (!ctx || !n_ops || !n_members || m < 1 || n < 1 || m > RR_MAX_SIDE || n > RR_MAX_SIDE || n_moves < 0 ||
+        n_moves > 0x3fffffff || (n_moves > 0 && !d_moves) || cap_ops < 0 || cap_members < 0)
+        return fail(ctx, RR_ERR_ARG, "rr_batch: bad argument (m=%d n=%d n_moves=%lld)", m, n, (long long)n_moves);
+    rr_instance h;
+    std::memset(&h, 0, sizeof(h));
+    h.grid = d_moves; h.layout = RR_U8; h.m = m; h.n = n;
+    h.rect = rr_rect{0, 0, m, n};
+    h.moves = const_cast<rr_move *>(d_moves); h.n_moves = n_moves; h.cap_moves = n_moves;
+    h.ops = d_ops; h.cap_ops = cap_ops; h.members = d_members; h.cap_members = cap_members;
+    h.status = RR_OK;
+    ctx->nmarks = 0;
+    CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_one, &h, sizeof(h), cudaMemcpyHostToDevice, stream));
+    int st = launch_batch(ctx, ctx->d_one, 1, std::max(m, n), stream);
+    if (st != RR_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(&h, ctx->d_one, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    *n_ops = h.n_ops;
+    *n_members = h.n_members;
+    if (h.status < 0) return fail(ctx, h.status, "rr_batch: device status %d", h.status);
+    return h.status;
+}
+
+extern "C" int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
+                               cudaStream_t stream)
+{
+    if (!ctx || !d_inst || count < 1 || count > 65535 || max_side < 1 || max_side > RR_MAX_SIDE ||
+        (flags & ~RR_WITH_BATCH))
+        return fail(ctx, RR_ERR_ARG, "rr_plan_batched: bad argument (count=%d max_side=%d flags=%d)", count,
+                    max_side, flags);
+    int st = ensure_ws(ctx, count);
+    if (st != RR_OK) return st;
+    ctx->nmarks = 0;
+    CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
+    st = launch_plan(ctx, d_inst, count, max_side, stream);
+    if (st != RR_OK) return st;
+    if (flags & RR_WITH_BATCH) st = launch_batch(ctx, d_inst, count, max_side, stream);
+    return st;
+}
+
+extern "C" int rr_set_tracing(rr_ctx *ctx, int enable)
+{
+    if (!ctx) return RR_ERR_ARG;
+    ctx->tracing = enable != 0;
+    ctx->nmarks = 0;
+    return RR_OK;
+}
+
+extern "C" int rr_stage_times(rr_ctx *ctx, float *ms, const char **names, int cap)
+{
+    if (!ctx || cap < 0 || (cap > 0 && (!ms || !names))) return fail(ctx, RR_ERR_ARG, "rr_stage_times: bad argument");
+    int n = 0;
+    for (int i = 0; i + 1 < ctx->nmarks && n < cap; ++i) {
+        if (!ctx->names[i]) continue;                 // end-of-sequence marker
+        CUDA_TRY(cudaEventSynchronize(ctx->marks[i + 1]));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, ctx->marks[i], ctx->marks[i + 1]));
+        ms[n] = t;
+        names[n] = ctx->names[i];
+        ++n;
+    }
+    return n;
+}

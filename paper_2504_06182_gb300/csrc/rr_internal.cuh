@@ -1,0 +1,154 @@
+// rr_internal.cuh -- device-side types and helpers shared by the kernels of
+// the red-rec planner and batching routine (arXiv 2504.06182, Alg. 1 and 2).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "rr.h"
+
+namespace rrk {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Column classification after the column phase (Alg. 1 first loop, solved for
+// every column of non-negative surplus at once as in Sec. III.D).
+enum ColKind : int32_t {
+    KIND_TARGET_SOLVED = 0,   // target column, surplus >= 0: exact 1D window solve
+    KIND_RECEIVER = 1,        // target column, surplus < 0
+    KIND_OUTER_FULL = 2,      // outside the target columns, enough atoms to fill its reservoir cells
+    KIND_OUTER_PART = 3       // outside the target columns, fewer atoms than reservoir cells
+};
+
+struct ColInfo {
+    int32_t K, ntop, nband, nbot;   // atoms: all, rows < r0, rows in [r0, r1), rows >= r1
+    int32_t sigma;                  // surplus after the column phase
+    int32_t kind;
+    int32_t ptop, pbot;             // donatable pool sizes (nearest-to-band first)
+    int32_t tbase, bbase;           // atom index of the nearest top / bottom pool atom
+    int32_t a;                      // target solved: top atoms taken into the window
+    int32_t kd_end, ku_start;       // solve order ranges (see emission)
+    int32_t nmoves;                 // moves of this column's column-phase unit
+    int32_t topRun, botRun;         // outer full: atoms already on their virtual targets
+};
+
+// One pairing iteration (Alg. 1 main loop).
+struct Event {
+    int32_t kase;       // 1: receiver saturated, 2: both saturated, 3: donor exhausted (delayed)
+    int32_t i, j;       // donor, receiver
+    int32_t x, a;       // tokens exchanged, of which a come from above the band
+    int32_t t0, b0;     // donor pool cursors (nearest-first index) before the exchange
+    int32_t next;       // next event with the same receiver, -1
+};
+
+// A receiver unit, in the order receivers become saturated.
+struct RecvInfo {
+    int32_t j;
+    int32_t ev_first;   // first event whose receiver is j (linked by Event::next)
+    int32_t ncontrib;   // events in that list
+    int32_t nT;         // sources above the band (mandatory + chosen)
+    int32_t kd_end, ku_start, nmoves;
+    int32_t pad;
+};
+
+struct Arena {
+    char *base;
+    unsigned long long size;
+    unsigned long long *top;   // device bump pointer
+};
+
+struct JobWS {
+    // planning
+    uint32_t *colbits;     // n * W, column-major bit columns (bit r & 31 of word r >> 5)
+    int16_t *atomRows;     // n * m: rows of the atoms of each column, ascending
+    int16_t *holeRows;     // n * h: rows of the empty band traps of each column, ascending
+    ColInfo *col;          // n
+    RecvInfo *recv;        // n
+    Event *ev;             // n + 1
+    int32_t *unitOff;      // 2n + 1
+    int32_t nrecv, nev;
+    // batching (Gamma + simulation)
+    int64_t P;             // total path vertices (sum of path length + 1)
+    int64_t E;             // successor entries
+    int32_t *pairOff;      // k + 1
+    int32_t *cellCnt;      // m * n + 1 (counts, then exclusive offsets)
+    int32_t *cellCur;      // m * n
+    int32_t *cover;        // P
+    int32_t *nextAt;       // P
+    int32_t *succOff;      // k + 1
+    int32_t *succ;         // E
+    int32_t *indeg;        // k
+    int32_t *pst;          // k * PST_STRIDE simulation state
+};
+
+constexpr int PST_STRIDE = 5;  // t, rowPrev, rowNext, colPrev, colNext
+
+__device__ __forceinline__ void *arena_alloc(const Arena &A, unsigned long long bytes, bool *ok)
+{
+    bytes = (bytes + 255ull) & ~255ull;
+    unsigned long long off = atomicAdd(A.top, bytes);
+    if (off + bytes > A.size) { *ok = false; return nullptr; }
+    return A.base + off;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum(int v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long u = __shfl_xor_sync(FULL, v, o);
+        v = u > v ? u : v;
+    }
+    return v;
+}
+
+// Bits of rows [lo, hi) that fall in word w (rows 32w .. 32w+31).
+__device__ __forceinline__ uint32_t row_mask(int w, int lo, int hi)
+{
+    int a = max(lo - 32 * w, 0), b = min(hi - 32 * w, 32);
+    if (b <= a) return 0u;
+    uint32_t hiMask = b >= 32 ? FULL : ((1u << b) - 1u);
+    uint32_t loMask = (1u << a) - 1u;
+    return hiMask & ~loMask;
+}
+
+__device__ __forceinline__ int iabs(int v) { return v < 0 ? -v : v; }
+__device__ __forceinline__ int isgn(int v) { return (v > 0) - (v < 0); }
+
+// Direction codes of rr_op.
+__device__ __forceinline__ int step_dir(int sr, int sc, int dr, int dc, int t)
+{
+    int hl = iabs(dc - sc);
+    if (t < hl) return dc > sc ? 3 : 2;
+    return dr > sr ? 1 : 0;
+}
+
+__device__ __forceinline__ void path_cell(int sr, int sc, int dr, int dc, int t, int *r, int *c)
+{
+    int hl = iabs(dc - sc);
+    if (t <= hl) { *r = sr; *c = sc + t * isgn(dc - sc); }
+    else { *r = sr + (t - hl) * isgn(dr - sr); *c = dc; }
+}
+
+// Status helpers: an instance is live while its status is RR_OK.
+__device__ __forceinline__ void set_status(rr_instance *I, int st)
+{
+    atomicCAS(&I->status, 0, st);
+}
+
+} // namespace rrk

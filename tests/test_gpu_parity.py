@@ -1,0 +1,223 @@
+"""GPU path against the oracle, element by element (bit-exact: all outputs
+are integers), through the C ABI.
+
+Sizes run from tiny random grids (several 32-wide tiles, ragged tails, odd
+rectangles) to the full workload shapes: one 32 x 32 and one 256 x 256 byte
+grid, mixed 32..256 bit-packed grids through the batched entry point, and
+one 1024 x 1024 bit-packed grid."""
+import os
+
+import numpy as np
+import pytest
+
+import gridgen
+import oracle
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def planner():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_06182_gb300.planner import Planner
+    p = Planner(arena_bytes=4 << 30)
+    yield p
+    p.close()
+
+
+def to_device(grid, layout):
+    from paper_2504_06182_gb300 import RR_U8
+    if layout == RR_U8:
+        return torch.from_numpy(np.ascontiguousarray(grid)).cuda()
+    words = gridgen.pack_bits32(grid).view(np.int32)
+    return torch.from_numpy(np.ascontiguousarray(words)).cuda()
+
+
+def gpu_plan(planner, grid, rect, layout):
+    m, n = grid.shape
+    st, mv = planner.plan(to_device(grid, layout), rect, layout=layout, n=n)
+    return st, mv.cpu().numpy()
+
+
+def check_instance(planner, grid, rect, layout, with_batch=True):
+    ref = oracle.plan(grid, rect)
+    st, mv = gpu_plan(planner, grid, rect, layout)
+    assert st == ref.status, (st, ref.status, grid.shape, rect)
+    assert mv.shape == ref.moves.shape, (mv.shape, ref.moves.shape)
+    if len(mv):
+        bad = np.nonzero((mv != ref.moves).any(axis=1))[0]
+        assert len(bad) == 0, f"first mismatch at move {bad[0]}: gpu {mv[bad[0]]} oracle {ref.moves[bad[0]]}"
+    if with_batch and ref.status == 0:
+        m, n = grid.shape
+        rops, rmem = oracle.batch(ref.moves, m, n)
+        ops, mem = planner.batch(torch.from_numpy(ref.moves).cuda(), m, n)
+        ops, mem = ops.cpu().numpy(), mem.cpu().numpy()
+        assert ops.shape == rops.shape, (ops.shape, rops.shape)
+        if len(ops):
+            bad = np.nonzero((ops != rops).any(axis=1))[0]
+            assert len(bad) == 0, f"first op mismatch at {bad[0]}: gpu {ops[bad[0]]} oracle {rops[bad[0]]}"
+        assert (mem == rmem).all()
+    return ref
+
+
+def random_case(rng):
+    m = int(rng.integers(1, 70))
+    n = int(rng.integers(1, 70))
+    grid = (rng.random((m, n)) < rng.uniform(0.2, 0.95)).astype(np.uint8)
+    h = int(rng.integers(1, m + 1))
+    r0 = int(rng.integers(0, m - h + 1))
+    w = int(rng.integers(1, n + 1))
+    c0 = int(rng.integers(0, n - w + 1))
+    return grid, (r0, c0, r0 + h, c0 + w)
+
+
+def test_random_small_grids(planner):
+    from paper_2504_06182_gb300 import RR_BITS32, RR_U8
+    rng = np.random.default_rng(1234)
+    feasible = 0
+    for trial in range(400):
+        grid, rect = random_case(rng)
+        ref = check_instance(planner, grid, rect, RR_U8 if trial % 2 else RR_BITS32, with_batch=trial % 4 == 0)
+        feasible += ref.status == 0
+    assert feasible > 100
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_grid_32_byte_layout(planner, seed):
+    from paper_2504_06182_gb300 import RR_U8
+    inst = gridgen.square_instance(seed, 0, 32, 0.6, 20)
+    check_instance(planner, inst.grid, inst.rect, RR_U8)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_grid_256_byte_layout(planner, seed):
+    from paper_2504_06182_gb300 import RR_U8
+    inst = gridgen.square_instance(seed, 0, 256, 0.6, 180)
+    ref = check_instance(planner, inst.grid, inst.rect, RR_U8)
+    assert ref.status == 0
+
+
+def test_edge_cases(planner):
+    from paper_2504_06182_gb300 import RR_BITS32, RR_U8
+    cases = []
+    cases.append((np.zeros((8, 8), np.uint8), (2, 2, 6, 6)))                 # no atoms: infeasible
+    cases.append((np.ones((8, 8), np.uint8), (2, 2, 6, 6)))                  # full grid
+    cases.append((np.ones((5, 7), np.uint8), (0, 0, 5, 7)))                  # target = whole grid
+    g = np.ones((6, 4), np.uint8); g[3, 1] = 0
+    cases.append((g, (0, 1, 6, 3)))                                          # h = m, one hole: infeasible
+    cases.append((np.ones((1, 1), np.uint8), (0, 0, 1, 1)))                  # 1 x 1
+    rng = np.random.default_rng(5)
+    cases.append(((rng.random((97, 1)) < 0.6).astype(np.uint8), (30, 0, 60, 1)))   # single column
+    cases.append(((rng.random((1, 97)) < 0.9).astype(np.uint8), (0, 3, 1, 90)))    # single row
+    cases.append(((rng.random((40, 33)) < 0.62).astype(np.uint8), (8, 0, 32, 33)))  # full width (paper geometry)
+    cases.append(((rng.random((65, 65)) < 0.6).astype(np.uint8), (10, 10, 55, 55)))  # ragged 32-tiles
+    chain = np.zeros((64, 1), np.uint8); chain[:32] = 1
+    cases.append((chain, (32, 0, 64, 1)))                                    # 2n-chain worst case
+    for i, (grid, rect) in enumerate(cases):
+        check_instance(planner, grid, rect, RR_U8 if i % 2 else RR_BITS32)
+
+
+def test_capacity_and_arguments(planner):
+    from paper_2504_06182_gb300 import RR_ERR_ARG, RR_ERR_CAPACITY, RR_U8, rr_plan
+    inst = gridgen.square_instance(1, 0, 32, 0.6, 20)
+    ref = oracle.plan(inst.grid, inst.rect)
+    g = to_device(inst.grid, RR_U8)
+    out = torch.full((10, 4), -7, dtype=torch.int32, device="cuda")
+    st, k = rr_plan(planner.ctx, g, RR_U8, 32, 32, inst.rect, out, 10)
+    assert st == RR_ERR_CAPACITY and k == len(ref.moves)
+    assert (out.cpu() == -7).all()                                           # nothing written
+    st, k = rr_plan(planner.ctx, g, RR_U8, 32, 32, (0, 0, 40, 32), out, 10)
+    assert st == RR_ERR_ARG
+    st, k = rr_plan(planner.ctx, g, 7, 32, 32, inst.rect, out, 10)
+    assert st == RR_ERR_ARG
+
+
+def test_batch_general_move_lists(planner):
+    """Alg. 2 on arbitrary unobstructed move sequences (not only red-rec output)."""
+    from tests.checks import replay_moves
+    rng = np.random.default_rng(99)
+    for trial in range(60):
+        m, n = int(rng.integers(2, 20)), int(rng.integers(2, 20))
+        g = (rng.random((m, n)) < 0.5).astype(np.uint8)
+        moves = []
+        for _ in range(80):
+            occ, free = np.argwhere(g == 1), np.argwhere(g == 0)
+            if not len(occ) or not len(free):
+                break
+            sr, sc = occ[rng.integers(len(occ))]
+            dr, dc = free[rng.integers(len(free))]
+            mv = (int(sr), int(sc), int(dr), int(dc))
+            try:
+                g = replay_moves(g, None, [mv])
+            except AssertionError:
+                continue
+            moves.append(mv)
+        if not moves:
+            continue
+        moves = np.array(moves, dtype=np.int32)
+        rops, rmem = oracle.batch(moves, m, n)
+        ops, mem = planner.batch(torch.from_numpy(moves).cuda(), m, n)
+        assert (ops.cpu().numpy() == rops).all() and (mem.cpu().numpy() == rmem).all()
+
+
+def test_batched_entry_point_mixed_sizes(planner):
+    """Mixed 32..256 bit-packed grids through one rr_plan_batched call with
+    batching, each compared with the oracle."""
+    from paper_2504_06182_gb300 import RR_BITS32, RR_ERR_CAPACITY, RR_INFEASIBLE, RR_OK
+    from paper_2504_06182_gb300.planner import pack_instances, plan_batched, unpack_instances
+    insts = gridgen.mixed_instances(11, 48)
+    refs = [oracle.plan(i.grid, i.rect) for i in insts]
+    entries, outs = [], []
+    for inst, ref in zip(insts, refs):
+        s = inst.grid.shape[0]
+        k = max(len(ref.moves), 1)
+        steps = int((np.abs(ref.moves[:, 0] - ref.moves[:, 2]) + np.abs(ref.moves[:, 1] - ref.moves[:, 3])).sum()) if len(ref.moves) else 0
+        mv = torch.empty((k, 4), dtype=torch.int32, device="cuda")
+        ops = torch.empty((max(steps, 1), 3), dtype=torch.int32, device="cuda")
+        mem = torch.empty((max(steps, 1),), dtype=torch.int32, device="cuda")
+        entries.append(dict(grid=to_device(inst.grid, RR_BITS32), layout=RR_BITS32, m=s, n=s, rect=inst.rect,
+                            moves=mv, cap_moves=k, ops=ops, cap_ops=max(steps, 1), members=mem,
+                            cap_members=max(steps, 1)))
+        outs.append((mv, ops, mem))
+    dev = pack_instances(entries)
+    plan_batched(planner, dev, len(entries), 256, with_batch=True)
+    torch.cuda.synchronize()
+    res = unpack_instances(dev, len(entries))
+    for inst, ref, r, (mv, ops, mem) in zip(insts, refs, res, outs):
+        assert r.status == (RR_OK if ref.status == 0 else RR_INFEASIBLE), r.status
+        assert r.n_moves == len(ref.moves)
+        if ref.status != 0:
+            continue
+        assert (mv[: r.n_moves].cpu().numpy() == ref.moves).all()
+        rops, rmem = oracle.batch(ref.moves, *inst.grid.shape)
+        assert r.n_ops == len(rops) and r.n_members == len(rmem)
+        assert (ops[: r.n_ops].cpu().numpy() == rops).all()
+        assert (mem[: r.n_members].cpu().numpy() == rmem).all()
+
+
+def test_grid_1024_bit_layout(planner):
+    """Full-size 1024 x 1024 grid with a centred 720 x 720 target: the whole
+    move list against the oracle, and the batches against the oracle (all of
+    them with RR_FULL_PARITY=1, else a leading sample) plus the conservation
+    of elementary steps over all of them."""
+    from paper_2504_06182_gb300 import RR_BITS32
+    inst = gridgen.square_instance(0, 0, 1024, 0.6, 720)
+    ref = oracle.plan(inst.grid, inst.rect)
+    st, mv = gpu_plan(planner, inst.grid, inst.rect, RR_BITS32)
+    assert st == 0 == ref.status
+    assert (mv == ref.moves).all()
+    ops, mem = planner.batch(torch.from_numpy(mv).cuda(), 1024, 1024)
+    ops, mem = ops.cpu().numpy(), mem.cpu().numpy()
+    steps = int((np.abs(mv[:, 0] - mv[:, 2]) + np.abs(mv[:, 1] - mv[:, 3])).sum())
+    assert len(mem) == steps == int(ops[:, 2].sum())
+    assert (ops[:, 1] == np.concatenate([[0], np.cumsum(ops[:, 2])[:-1]])).all()
+    if os.environ.get("RR_FULL_PARITY") == "1":
+        rops, rmem = oracle.batch(ref.moves, 1024, 1024)
+        assert (ops == rops).all() and (mem == rmem).all()
+    else:
+        rops, rmem = oracle.batch(ref.moves, 1024, 1024, max_ops=200000)
+        assert (ops[: len(rops)] == rops).all()
+        assert (mem[: len(rmem)] == rmem).all()
