@@ -79,6 +79,8 @@ def oracle_sample(insts, budget_s, threads):
                 pending.add(ex.submit(one, x))
         while pending:
             fin, pending = cf.wait(pending, return_when=cf.FIRST_COMPLETED)
+            for f in fin:
+                f.result()              # re-raise oracle failures
             done += len(fin)
             if time.perf_counter() - t0 < budget_s:
                 for _ in fin:

@@ -182,8 +182,10 @@ static int tok_push(tokvec_t *T, tok_t t)
     return OK;
 }
 
-/* Order of tokens projected onto receiver column g_rcv (see header). */
-static int g_r0, g_r1, g_rcv, g_tie_bug;
+/* Order of tokens projected onto receiver column g_rcv (see header). The
+ * comparator's parameters are thread-local so that concurrent calls (the CPU
+ * baseline runs the oracle on several host threads) do not interfere. */
+static _Thread_local int g_r0, g_r1, g_rcv, g_tie_bug;
 static int cmp_tok(const void *pa, const void *pb)
 {
     const tok_t *a = (const tok_t *)pa, *b = (const tok_t *)pb;

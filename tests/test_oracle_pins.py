@@ -307,3 +307,15 @@ def test_outer_columns_only_vertical_in_column_phase():
         assert ((L[:, 0] < r0) | (L[:, 0] >= r1)).all()
         assert ((L[:, 2] >= r0) & (L[:, 2] < r1)).all()
         assert ((L[:, 3] >= c0) & (L[:, 3] < c1)).all()
+
+
+def test_oracle_reentrant_across_threads():
+    """Concurrent oracle calls (the CPU baseline uses a thread pool) give the
+    same plans as sequential ones."""
+    import concurrent.futures as cf
+    insts = gridgen.mixed_instances(21, 24, sides=(32, 48, 64, 96), p_lo=0.55, p_hi=0.7)
+    seq = [oracle.plan(i.grid, i.rect).moves for i in insts]
+    with cf.ThreadPoolExecutor(8) as ex:
+        par = list(ex.map(lambda i: oracle.plan(i.grid, i.rect).moves, insts * 3))
+    for a, b in zip(seq * 3, par):
+        assert a.shape == b.shape and (a == b).all()
