@@ -124,7 +124,10 @@ __global__ void k_bsetup(rr_instance *inst, JobWS *wsv, int count, Arena A)
             ws.nextAt = (int32_t *)arena_alloc(A, 4ull * (tp + 1), &ok);
             ws.succOff = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
             ws.indeg = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
-            ws.pst = (int32_t *)arena_alloc(A, 4ull * PST_STRIDE * (k + 1) + 4ull * ((k + 32) / 32), &ok);
+            ws.rec = (int4 *)arena_alloc(A, 16ull * (k + 1), &ok);
+            ws.succ4 = (int4 *)arena_alloc(A, 16ull * (k + 1), &ok);
+            ws.ready0 = (int32_t *)arena_alloc(A, 4ull * (k + 1) + 16, &ok);
+            ws.slotOvf = arena_alloc(A, 64ull * (k + 1), &ok);
             ws.succ = nullptr; ws.E = 0;
             if (!ok) I->status = RR_ERR_WORKSPACE;
         }
@@ -136,11 +139,8 @@ __global__ void k_bsetup(rr_instance *inst, JobWS *wsv, int count, Arena A)
         const rr_move p = I->moves[b];
         ws.pairOff[b] = iabs(p.dst_col - p.src_col) + iabs(p.dst_row - p.src_row) + 1;
         ws.indeg[b] = 0;
-        int32_t *ps = ws.pst + PST_STRIDE * b;
-        ps[0] = 0; ps[1] = -1; ps[2] = -1; ps[3] = -1; ps[4] = -1;
     }
-    uint32_t *done = (uint32_t *)(ws.pst + PST_STRIDE * (k + 1));
-    for (int64_t w = threadIdx.x; w < (k + 32) / 32; w += blockDim.x) done[w] = 0u;
+    if (threadIdx.x == 0) ws.ready0[k] = 0;      // count of initially ready moves
     const long long cells = (long long)m * n;
     for (long long v = threadIdx.x; v < cells; v += blockDim.x) { ws.cellCnt[v] = 0; ws.cellCur[v] = 0; }
     __syncthreads();
@@ -307,129 +307,237 @@ __global__ void k_bsucc_fill(rr_instance *inst, JobWS *wsv, int count)
     }
 }
 
-// ---------------------------------------------------------- simulation
-
-struct SimSmem {
-    int32_t *rowHead;   // [4][m]
-    int32_t *colHead;   // [4][n]
-    uint32_t *rowBits;  // [2][Wm] dirs 0,1 : rows with a waiting move of that direction
-    uint32_t *colBits;  // [2][Wn] dirs 2,3 : columns with a waiting move of that direction
-    int32_t *S;         // batch members
-    int m, n, Wm, Wn;
-};
-
-struct PathGeo {
-    int sr, sc, dr, dc, len, hl;
-};
-
-__device__ __forceinline__ PathGeo load_geo(const rr_move *mv, int p)
+// Per-move records for the simulation: packed geometry, successor count and
+// the first four successors (flagged when the successor has no other
+// predecessor); later successors are flagged in place. Moves without
+// predecessors are listed as initially ready.
+__global__ void k_brec(rr_instance *inst, JobWS *wsv, int count)
 {
-    const rr_move x = mv[p];
-    PathGeo g;
-    g.sr = x.src_row; g.sc = x.src_col; g.dr = x.dst_row; g.dc = x.dst_col;
-    g.hl = iabs(g.dc - g.sc);
-    g.len = g.hl + iabs(g.dr - g.sr);
-    return g;
-}
-
-__device__ __forceinline__ void geo_at(const PathGeo &g, int t, int *d, int *r, int *c, int *rem)
-{
-    if (t < g.hl) { *d = g.dc > g.sc ? 3 : 2; *r = g.sr; *c = g.sc + t * isgn(g.dc - g.sc); *rem = g.hl - t; }
-    else { *d = g.dr > g.sr ? 1 : 0; *r = g.sr + (t - g.hl) * isgn(g.dr - g.sr); *c = g.dc; *rem = g.len - t; }
-}
-
-__device__ __forceinline__ void bit_set(uint32_t *b, int i) { b[i >> 5] |= 1u << (i & 31); }
-__device__ __forceinline__ void bit_clr(uint32_t *b, int i) { b[i >> 5] &= ~(1u << (i & 31)); }
-
-// Lists of waiting ready moves per (direction, row) and (direction, column).
-__device__ void line_insert(SimSmem &S, int32_t *pst, int p, int d, int r, int c)
-{
-    int32_t *ps = pst + PST_STRIDE * p;
-    int32_t *hr = &S.rowHead[d * S.m + r];
-    ps[1] = -1; ps[2] = *hr;
-    if (*hr >= 0) pst[PST_STRIDE * *hr + 1] = p;
-    *hr = p;
-    int32_t *hc = &S.colHead[d * S.n + c];
-    ps[3] = -1; ps[4] = *hc;
-    if (*hc >= 0) pst[PST_STRIDE * *hc + 3] = p;
-    *hc = p;
-    if (d < 2) bit_set(S.rowBits + d * S.Wm, r); else bit_set(S.colBits + (d - 2) * S.Wn, c);
-}
-
-__device__ void line_remove(SimSmem &S, int32_t *pst, int p, int d, int r, int c)
-{
-    int32_t *ps = pst + PST_STRIDE * p;
-    const int rp = ps[1], rn = ps[2], cp = ps[3], cn = ps[4];
-    if (rp >= 0) pst[PST_STRIDE * rp + 2] = rn; else S.rowHead[d * S.m + r] = rn;
-    if (rn >= 0) pst[PST_STRIDE * rn + 1] = rp;
-    if (cp >= 0) pst[PST_STRIDE * cp + 4] = cn; else S.colHead[d * S.n + c] = cn;
-    if (cn >= 0) pst[PST_STRIDE * cn + 3] = cp;
-    if (d < 2) { if (S.rowHead[d * S.m + r] < 0) bit_clr(S.rowBits + d * S.Wm, r); }
-    else { if (S.colHead[d * S.n + c] < 0) bit_clr(S.colBits + (d - 2) * S.Wn, c); }
-}
-
-// First i in 1..maxq with bit (pos + i*delta) set, or 0.
-__device__ int bit_scan(const uint32_t *b, int limit, int pos, int delta, int maxq)
-{
-    for (int i = 1; i <= maxq; ++i) {
-        const int x = pos + i * delta;
-        if (x < 0 || x >= limit) return 0;
-        const uint32_t w = b[x >> 5];
-        if (w == 0u) {
-            // skip the rest of an empty word
-            const int edge = delta > 0 ? ((x | 31) - pos) : (pos - (x & ~31));
-            i = edge;
-            continue;
+    const int q = blockIdx.y;
+    if (q >= count) return;
+    const rr_instance *I = &inst[q];
+    if (!live(I)) return;
+    JobWS &ws = wsv[q];
+    const int64_t k = I->n_moves;
+    for (int64_t b = blockIdx.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)gridDim.x * blockDim.x) {
+        const rr_move p = I->moves[b];
+        const int lo = ws.succOff[b], hi = ws.succOff[b + 1];
+        int4 r;
+        r.x = (p.src_row & 0xffff) | (p.src_col << 16);
+        r.y = (p.dst_row & 0xffff) | (p.dst_col << 16);
+        r.z = hi - lo;
+        r.w = lo + 4;
+        int v[4] = {-1, -1, -1, -1};
+        for (int e = lo; e < hi; ++e) {
+            const int32_t sId = ws.succ[e];
+            const int32_t f = sId | (ws.indeg[sId] == 1 ? SUCC_SINGLE : 0);
+            if (e - lo < 4) v[e - lo] = f; else ws.succ[e] = f;
         }
-        if ((w >> (x & 31)) & 1u) return i;
+        ws.rec[b] = r;
+        ws.succ4[b] = make_int4(v[0], v[1], v[2], v[3]);
+        if (ws.indeg[b] == 0) ws.ready0[atomicAdd(&ws.ready0[k], 1)] = (int32_t)b;
     }
-    return 0;
 }
 
-__global__ void k_sim(rr_instance *inst, JobWS *wsv, int count)
+// ---------------------------------------------------------- simulation
+//
+// The ready moves live in a slot table (structure of arrays). Slots below
+// the shared-memory capacity are in shared memory, the rest in a global
+// overflow area with the same layout. Each batch is composed by one
+// warp-wide pass over the slot table: every lane tests its slots against the
+// leader's row and column for the leader's direction, giving both candidate
+// lines with their smallest ids, their members (as ballot masks), their
+// shortest remaining straight leg, and the distance to the nearest waiting
+// move of the same direction that the leader's line will reach.
+
+constexpr int MAPN = 1024;      // id -> slot cache for finding the next leader
+constexpr int SBUF = 512;       // successor entries released per round
+constexpr int KEY_LIVE = 1 << 22;
+
+struct SlotSoA {
+    int32_t *key;     // row | col << 10 | dir << 20 | KEY_LIVE; 0 when free
+    int32_t *id;      // move id, INT_MAX when free
+    int32_t *g0, *g1; // src_row | src_col << 16, dst_row | dst_col << 16
+    int32_t *t;       // elementary steps done
+    int32_t *legEnd;  // t at the end of the current straight leg
+    int32_t *nsucc, *ovf;
+    int4 *s4;         // first four successors
+};
+
+struct Sim {
+    SlotSoA sm, gm;
+    int C;
+    int32_t *freeStk;
+    int32_t *map;
+    int32_t *M;                 // member slots of the current batch, sorted by id
+    long long *Mk;              // sort keys (id << 32 | slot)
+    uint32_t *maskA, *maskB;    // ballot masks of the two candidate lines
+    int32_t *sbuf;
+    int4 *stRec, *stS4;
+    int32_t *newIds;
+};
+
+#define SLOTF(X, f, i) (*((i) < (X).C ? &(X).sm.f[(i)] : &(X).gm.f[(i) - (X).C]))
+
+__device__ __forceinline__ int key_of(int r, int c, int d) { return r | (c << 10) | (d << 20) | KEY_LIVE; }
+
+// Position, direction and remaining straight leg after t steps of a move.
+__device__ __forceinline__ void move_pos(int g0, int g1, int t, int *r, int *c, int *d, int *rem, int *len)
 {
-    extern __shared__ int32_t smem_i32[];
+    const int sr = g0 & 0xffff, sc = g0 >> 16, dr = g1 & 0xffff, dc = g1 >> 16;
+    const int hl = iabs(dc - sc);
+    *len = hl + iabs(dr - sr);
+    if (t < hl) { *d = dc > sc ? 3 : 2; *r = sr; *c = sc + (dc > sc ? t : -t); *rem = hl - t; }
+    else { const int v = t - hl; *d = dr > sr ? 1 : 0; *r = sr + (dr > sr ? v : -v); *c = dc; *rem = *len - t; }
+}
+
+__device__ __forceinline__ int warp_min(int v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+// Lowest move id held in slots [0, hi) and its slot (warp-cooperative).
+__device__ int lowest_slot(const Sim &X, int hi)
+{
+    const int lane = threadIdx.x & 31;
+    int best = 0x7fffffff, bs = -1;
+    for (int i = lane; i < hi; i += 32) {
+        const int id = SLOTF(X, id, i);
+        if (id < best) { best = id; bs = i; }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const int ob = __shfl_xor_sync(FULL, best, o), os = __shfl_xor_sync(FULL, bs, o);
+        if (ob < best || (ob == best && os < bs)) { best = ob; bs = os; }
+    }
+    return best == 0x7fffffff ? -1 : bs;
+}
+
+// Sort Mk[0..n) ascending (warp-cooperative bitonic sort in shared memory).
+__device__ void warp_sort64(long long *a, int n)
+{
+    const int lane = threadIdx.x & 31;
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = n + lane; i < P; i += 32) a[i] = 0x7fffffffffffffffll;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < P; i += 32) {
+                const int ij = i ^ j;
+                if (ij > i) {
+                    const long long x = a[i], y = a[ij];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) { a[i] = y; a[ij] = x; }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Allocate `cnt` slots (warp-cooperative); returns this lane's slot for
+// rank < cnt. freeTop / ovfUsed / hi are warp-uniform.
+__device__ __forceinline__ int alloc_slot(const Sim &X, int rank, int cnt, int &freeTop, int &ovfUsed, int &hi,
+                                          int kmax, int *err)
+{
+    int si = -1;
+    const int fromStack = min(cnt, freeTop);
+    if (rank < fromStack) si = X.freeStk[freeTop - 1 - rank];
+    else if (rank < cnt) si = X.C + ovfUsed + (rank - fromStack);
+    freeTop -= fromStack;
+    ovfUsed += cnt - fromStack;
+    if (ovfUsed > kmax) *err = RR_ERR_INTERNAL;
+    int top = si + 1;
+    top = max(top, __shfl_xor_sync(FULL, top, 16)); top = max(top, __shfl_xor_sync(FULL, top, 8));
+    top = max(top, __shfl_xor_sync(FULL, top, 4)); top = max(top, __shfl_xor_sync(FULL, top, 2));
+    top = max(top, __shfl_xor_sync(FULL, top, 1));
+    hi = max(hi, top);
+    return si;
+}
+
+__device__ __forceinline__ void fill_slot(const Sim &X, int si, int id, int4 r, int4 s4)
+{
+    int rr, cc, d, rem, len;
+    move_pos(r.x, r.y, 0, &rr, &cc, &d, &rem, &len);
+    SLOTF(X, key, si) = key_of(rr, cc, d);
+    SLOTF(X, id, si) = id;
+    SLOTF(X, g0, si) = r.x;
+    SLOTF(X, g1, si) = r.y;
+    SLOTF(X, t, si) = 0;
+    SLOTF(X, legEnd, si) = rem;
+    SLOTF(X, nsucc, si) = r.z;
+    SLOTF(X, ovf, si) = r.w;
+    SLOTF(X, s4, si) = s4;
+    X.map[id & (MAPN - 1)] = si;
+}
+
+__global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int lineCap)
+{
+    extern __shared__ int4 smem_i4[];
     const int q = blockIdx.x;
     if (q >= count) return;
     rr_instance *I = &inst[q];
     if (!live(I)) return;
     JobWS &ws = wsv[q];
-    const int m = I->m, n = I->n;
     const int k = (int)I->n_moves;
     const int lane = threadIdx.x & 31;
     if (k == 0) { if (lane == 0) { I->n_ops = 0; I->n_members = 0; } return; }
 
-    SimSmem S;
-    S.m = m; S.n = n; S.Wm = (m + 31) >> 5; S.Wn = (n + 31) >> 5;
-    S.rowHead = smem_i32;
-    S.colHead = S.rowHead + 4 * m;
-    S.rowBits = (uint32_t *)(S.colHead + 4 * n);
-    S.colBits = S.rowBits + 2 * S.Wm;
-    S.S = (int32_t *)(S.colBits + 2 * S.Wn);
-    for (int i = lane; i < 4 * m; i += 32) S.rowHead[i] = -1;
-    for (int i = lane; i < 4 * n; i += 32) S.colHead[i] = -1;
-    for (int i = lane; i < 2 * S.Wm; i += 32) S.rowBits[i] = 0u;
-    for (int i = lane; i < 2 * S.Wn; i += 32) S.colBits[i] = 0u;
+    // shared-memory layout (mirrored by the launcher's size computation)
+    Sim X;
+    X.C = slotCap;
+    X.sm.s4 = smem_i4;
+    X.stRec = X.sm.s4 + slotCap;
+    X.stS4 = X.stRec + 32;
+    X.Mk = (long long *)(X.stS4 + 32);
+    int32_t *p32 = (int32_t *)(X.Mk + 2 * (lineCap + 2));
+    X.sm.key = p32; p32 += slotCap;
+    X.sm.id = p32; p32 += slotCap;
+    X.sm.g0 = p32; p32 += slotCap;
+    X.sm.g1 = p32; p32 += slotCap;
+    X.sm.t = p32; p32 += slotCap;
+    X.sm.legEnd = p32; p32 += slotCap;
+    X.sm.nsucc = p32; p32 += slotCap;
+    X.sm.ovf = p32; p32 += slotCap;
+    X.freeStk = p32; p32 += slotCap;
+    X.map = p32; p32 += MAPN;
+    X.M = p32; p32 += lineCap + 2;
+    X.sbuf = p32; p32 += SBUF;
+    X.newIds = p32; p32 += 32;
+    X.maskA = (uint32_t *)p32; p32 += 64;
+    X.maskB = (uint32_t *)p32; p32 += 64;
+    // overflow slots (global), same structure
+    {
+        char *g = (char *)ws.slotOvf;
+        const size_t K1 = (size_t)k + 1;
+        X.gm.s4 = (int4 *)g;               g += 16 * K1;
+        X.gm.key = (int32_t *)g;           g += 4 * K1;
+        X.gm.id = (int32_t *)g;            g += 4 * K1;
+        X.gm.g0 = (int32_t *)g;            g += 4 * K1;
+        X.gm.g1 = (int32_t *)g;            g += 4 * K1;
+        X.gm.t = (int32_t *)g;             g += 4 * K1;
+        X.gm.legEnd = (int32_t *)g;        g += 4 * K1;
+        X.gm.nsucc = (int32_t *)g;         g += 4 * K1;
+        X.gm.ovf = (int32_t *)g;
+    }
+    for (int i = lane; i < slotCap; i += 32) { X.sm.key[i] = 0; X.sm.id[i] = 0x7fffffff; X.freeStk[i] = slotCap - 1 - i; }
+    for (int i = lane; i < MAPN; i += 32) X.map[i] = -1;
+    int freeTop = slotCap, ovfUsed = 0, hi = 0, err = 0;
     __syncwarp();
 
-    int32_t *pst = ws.pst;
-    uint32_t *done = (uint32_t *)(ws.pst + PST_STRIDE * (k + 1));
-    const rr_move *mv = I->moves;
-    const int32_t *indeg0 = ws.indeg;
-    // initially ready moves (in-degree 0), inserted by lane 0 in id order
-    for (int base = 0; base < k; base += 32) {
-        const int b = base + lane;
-        const unsigned bal = __ballot_sync(FULL, b < k && indeg0[b] == 0);
-        if (lane == 0) {
-            unsigned x = bal;
-            while (x) {
-                const int p = base + __ffs(x) - 1;
-                x &= x - 1;
-                const PathGeo g = load_geo(mv, p);
-                int d, r, c, rem; geo_at(g, 0, &d, &r, &c, &rem);
-                line_insert(S, pst, p, d, r, c);
-            }
-        }
+    // moves without predecessors
+    const int32_t *ready0 = ws.ready0;
+    const int nready0 = ready0[k];
+    for (int base = 0; base < nready0; base += 32) {
+        const int cnt = min(32, nready0 - base);
+        int id = -1;
+        int4 r = make_int4(0, 0, 0, 0), s4 = r;
+        if (lane < cnt) { id = ready0[base + lane]; r = ws.rec[id]; s4 = ws.succ4[id]; }
+        const int si = alloc_slot(X, lane, cnt, freeTop, ovfUsed, hi, k, &err);
+        if (lane < cnt) fill_slot(X, si, id, r, s4);
         __syncwarp();
     }
 
@@ -437,157 +545,211 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count)
     rr_op *ops = I->ops;
     int32_t *mem = I->members;
     int64_t nop = 0, nmem = 0;
-    int overflow = 0, err = 0;
-
-    // leader state (kept uniform across the warp via lane-0 broadcasts)
-    int L = 0;
-    PathGeo Lg = load_geo(mv, 0);
-    int Lt = 0;
-    if (lane == 0) {
-        if (indeg0[0] != 0) err = RR_ERR_INTERNAL;
-        int d, r, c, rem; geo_at(Lg, 0, &d, &r, &c, &rem);
-        line_remove(S, pst, 0, d, r, c);
-    }
-    err = __shfl_sync(FULL, err, 0);
-    const int64_t guard_max = I->n_steps + (int64_t)k + 16;
+    int overflow = 0;
+    int Ls = lowest_slot(X, hi);
+    int L = Ls >= 0 ? SLOTF(X, id, Ls) : -1;
+    if (L != 0) err = RR_ERR_INTERNAL;
+    const int64_t guard_max = I->n_steps + 2ll * k + 16;
     int64_t guard = 0;
 
     while (!err && L < k) {
         if (++guard > guard_max) { err = RR_ERR_TIMEOUT; break; }
-        int ns = 0, d = 0, kseg = 0;
-        if (lane == 0) {
-            int r, c, remL; geo_at(Lg, Lt, &d, &r, &c, &remL);
-            // candidates on the leader's row (A) and column (B)
-            // a line holds at most one token per trap: walks longer than that
-            // mean a corrupted list and end the simulation with an error
-            const int lineCap = max(m, n);
-            int minA = 0x7fffffff, minB = 0x7fffffff, walk = 0;
-            for (int p = S.rowHead[d * m + r]; p >= 0 && walk <= lineCap; p = pst[PST_STRIDE * p + 2], ++walk)
-                minA = min(minA, p);
-            for (int p = S.colHead[d * n + c]; p >= 0 && walk <= 2 * lineCap; p = pst[PST_STRIDE * p + 4], ++walk)
-                minB = min(minB, p);
-            if (walk > 2 * lineCap) err = RR_ERR_INTERNAL;
-            S.S[0] = L; ns = 1;
-            kseg = remL;
-            if (!err && (minA != 0x7fffffff || minB != 0x7fffffff)) {
-                const bool useA = minA < minB;
-                for (int p = useA ? S.rowHead[d * m + r] : S.colHead[d * n + c]; p >= 0 && ns <= lineCap;
-                     p = pst[PST_STRIDE * p + (useA ? 2 : 4)])
-                    S.S[ns++] = p;
-                for (int u = 1; u < ns; ++u) {
-                    const int p = S.S[u];
-                    const PathGeo g = load_geo(mv, p);
-                    int dd, rr, cc, rem; geo_at(g, pst[PST_STRIDE * p], &dd, &rr, &cc, &rem);
-                    kseg = min(kseg, rem);
-                }
-                for (int u = 1; u < ns; ++u) {
-                    const int p = S.S[u];
-                    const PathGeo g = load_geo(mv, p);
-                    int dd, rr, cc, rem; geo_at(g, pst[PST_STRIDE * p], &dd, &rr, &cc, &rem);
-                    line_remove(S, pst, p, dd, rr, cc);
-                }
-                // members in ascending id (insertion sort; batches are short)
-                for (int u = 2; u < ns; ++u) {
-                    const int x = S.S[u];
-                    int v = u - 1;
-                    while (v >= 1 && S.S[v] > x) { S.S[v + 1] = S.S[v]; --v; }
-                    S.S[v + 1] = x;
+        // leader state (uniform)
+        int lr, lc, d, remL, lenL;
+        const int Lg0 = SLOTF(X, g0, Ls), Lg1 = SLOTF(X, g1, Ls), Lt = SLOTF(X, t, Ls);
+        move_pos(Lg0, Lg1, Lt, &lr, &lc, &d, &remL, &lenL);
+        const int sgn = (d == 1 || d == 3) ? 1 : -1;
+        // one pass over the slot table (shared-memory part unrolled for
+        // memory-level parallelism, overflow part after it)
+        int minA = 0x7fffffff, minB = 0x7fffffff, pickA = 0x7fffffff, pickB = 0x7fffffff;
+        int remA = 0x7fffffff, remB = 0x7fffffff;
+        const int nwords = (hi + 31) >> 5;
+        auto visit = [&](int key, int i, int w) {
+            const bool same = (key & KEY_LIVE) && ((key >> 20) & 3) == d && i != Ls;
+            const int sr = key & 1023, sc = (key >> 10) & 1023;
+            const bool inA = same && sr == lr, inB = same && sc == lc;
+            if (inA || inB) {
+                const int id = SLOTF(X, id, i);
+                const int rem = SLOTF(X, legEnd, i) - SLOTF(X, t, i);
+                if (inA) { minA = min(minA, id); remA = min(remA, rem); }
+                if (inB) { minB = min(minB, id); remB = min(remB, rem); }
+            }
+            if (same) {
+                const int dist = (d >= 2 ? sc - lc : sr - lr) * sgn;
+                if (dist > 0) {
+                    if (!inA) pickA = min(pickA, dist);
+                    if (!inB) pickB = min(pickB, dist);
                 }
             }
-            // a waiting move of direction d that the leader's line reaches
-            if (kseg > 1) {
-                int hit;
-                if (d >= 2) hit = bit_scan(S.colBits + (d - 2) * S.Wn, n, c, d == 3 ? 1 : -1, kseg - 1);
-                else hit = bit_scan(S.rowBits + d * S.Wm, m, r, d == 1 ? 1 : -1, kseg - 1);
-                if (hit > 0) kseg = hit;
-            }
+            const unsigned bA = __ballot_sync(FULL, inA), bB = __ballot_sync(FULL, inB);
+            if (lane == 0) { X.maskA[w] = bA; X.maskB[w] = bB; }
+        };
+        const int hs = min(hi, X.C);
+        const int wsm = (hs + 31) >> 5;
+        int w = 0;
+        for (; w + 4 <= wsm; w += 4) {
+            int kk[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { const int i = 32 * (w + u) + lane; kk[u] = i < hs ? X.sm.key[i] : 0; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) visit(kk[u], 32 * (w + u) + lane, w + u);
         }
-        ns = __shfl_sync(FULL, ns, 0);
-        d = __shfl_sync(FULL, d, 0);
-        kseg = __shfl_sync(FULL, kseg, 0);
-        err = __shfl_sync(FULL, err, 0);
+        for (; w < nwords; ++w) {
+            const int i = 32 * w + lane;
+            visit(i < hi ? SLOTF(X, key, i) : 0, i, w);
+        }
+        minA = warp_min(minA); minB = warp_min(minB);
+        pickA = warp_min(pickA); pickB = warp_min(pickB);
+        remA = warp_min(remA); remB = warp_min(remB);
+        const bool any = minA != 0x7fffffff || minB != 0x7fffffff;
+        const bool useA = minA < minB;
+        int kseg = remL;
+        if (any) kseg = min(kseg, useA ? remA : remB);
+        kseg = min(kseg, useA || !any ? pickA : pickB);
         __syncwarp();
-        if (err) break;
+        // members: the leader, then the chosen line in ascending id
+        int ns = 1;
+        if (any) {
+            const uint32_t *mask = useA ? X.maskA : X.maskB;
+            int carry = 0;
+            for (int wb = 0; wb < nwords; wb += 32) {
+                const int w = wb + lane;
+                const uint32_t bits = w < nwords ? mask[w] : 0u;
+                const int c = __popc(bits);
+                const int incl = warp_incl_scan(c);
+                int pos = carry + incl - c;
+                uint32_t b = bits;
+                while (b) {
+                    const int i = 32 * w + __ffs(b) - 1;
+                    b &= b - 1;
+                    X.Mk[pos++] = ((long long)SLOTF(X, id, i) << 32) | (unsigned)i;
+                }
+                carry += __shfl_sync(FULL, incl, 31);
+            }
+            __syncwarp();
+            if (carry > lineCap) { err = RR_ERR_INTERNAL; break; }
+            if (carry <= 32) {
+                // bitonic sort across the warp's registers
+                long long v = lane < carry ? X.Mk[lane] : 0x7fffffffffffffffll;
+#pragma unroll
+                for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+                    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                        const long long o = __shfl_xor_sync(FULL, v, jj);
+                        const bool up = (lane & kk) == 0, low = (lane & jj) == 0;
+                        v = (low == up) ? (v < o ? v : o) : (v > o ? v : o);
+                    }
+                }
+                if (lane < carry) { X.Mk[lane] = v; X.M[1 + lane] = (int)(v & 0xffffffff); }
+            } else {
+                warp_sort64(X.Mk, carry);
+                for (int u = lane; u < carry; u += 32) X.M[1 + u] = (int)(X.Mk[u] & 0xffffffff);
+            }
+            ns = 1 + carry;
+        }
+        if (lane == 0) X.M[0] = Ls;
+        __syncwarp();
         if (kseg < 1) { err = RR_ERR_INTERNAL; break; }
-        // write kseg identical batches
+        // kseg identical batches
         const int64_t addm = (int64_t)kseg * ns;
         if (!overflow && nop + kseg <= cap_ops && nmem + addm <= cap_mem) {
             for (int i = lane; i < kseg; i += 32) ops[nop + i] = rr_op{d, (int32_t)(nmem + (int64_t)i * ns), ns};
             if (ns == 1) {
                 for (int i = lane; i < kseg; i += 32) mem[nmem + i] = L;
             } else {
-                for (int64_t i = lane; i < addm; i += 32) mem[nmem + i] = S.S[i % ns];
+                // member u of every batch: the leader, then the sorted line
+                int u = lane % ns;
+                const int step = 32 % ns;
+                for (int64_t i = lane; i < addm; i += 32) {
+                    mem[nmem + i] = u == 0 ? L : (int)(X.Mk[u - 1] >> 32);
+                    u += step;
+                    if (u >= ns) u -= ns;
+                }
             }
         } else {
             overflow = 1;
         }
         nop += kseg;
         nmem += addm;
-        __syncwarp();
-        // advance members, retire finished moves, reinsert the others
-        int newL = L;
-        if (lane == 0) {
-            for (int u = 1; u < ns; ++u) {
-                const int p = S.S[u];
-                const PathGeo g = load_geo(mv, p);
-                const int t = pst[PST_STRIDE * p] + kseg;
-                pst[PST_STRIDE * p] = t;
-                if (t >= g.len) {
-                    done[p >> 5] |= 1u << (p & 31);
-                    for (int e = ws.succOff[p]; e < ws.succOff[p + 1]; ++e) {
-                        const int s = ws.succ[e];
-                        if (atomicSub(&ws.indeg[s], 1) == 1) {
-                            const PathGeo gs = load_geo(mv, s);
-                            int dd, rr, cc, rem; geo_at(gs, pst[PST_STRIDE * s], &dd, &rr, &cc, &rem);
-                            line_insert(S, pst, s, dd, rr, cc);
-                        }
-                    }
-                } else {
-                    int dd, rr, cc, rem; geo_at(g, t, &dd, &rr, &cc, &rem);
-                    line_insert(S, pst, p, dd, rr, cc);
-                }
+
+        // advance every member; finished ones release their successors
+        int leaderDone = 0;
+        for (int u0 = 0; u0 < ns; u0 += 32) {
+            const int u = u0 + lane;
+            bool fin = false;
+            int si = -1, nsu = 0;
+            if (u < ns) {
+                si = X.M[u];
+                const int t = SLOTF(X, t, si) + kseg;
+                int r_, c_, d_, rem, len;
+                move_pos(SLOTF(X, g0, si), SLOTF(X, g1, si), t, &r_, &c_, &d_, &rem, &len);
+                SLOTF(X, t, si) = t;
+                if (t >= len) { fin = true; nsu = SLOTF(X, nsucc, si); }
+                else { SLOTF(X, key, si) = key_of(r_, c_, d_); SLOTF(X, legEnd, si) = t + rem; }
             }
-            Lt += kseg;
-            if (Lt >= Lg.len) {
-                pst[PST_STRIDE * L] = Lt;
-                done[L >> 5] |= 1u << (L & 31);
-                for (int e = ws.succOff[L]; e < ws.succOff[L + 1]; ++e) {
-                    const int s = ws.succ[e];
-                    if (atomicSub(&ws.indeg[s], 1) == 1) {
-                        const PathGeo gs = load_geo(mv, s);
-                        int dd, rr, cc, rem; geo_at(gs, pst[PST_STRIDE * s], &dd, &rr, &cc, &rem);
-                        line_insert(S, pst, s, dd, rr, cc);
+            if (__shfl_sync(FULL, (int)fin, 0) && u0 == 0) leaderDone = 1;
+            // successor entries of the finished members, in rounds of SBUF
+            int off = warp_incl_scan(nsu) - nsu;
+            const int total = __shfl_sync(FULL, off + nsu, 31);
+            for (int base = 0; base < total; base += SBUF) {
+                if (fin) {
+                    for (int e = max(0, base - off); e < nsu && off + e < base + SBUF; ++e) {
+                        const int4 s4 = SLOTF(X, s4, si);
+                        const int v = e == 0 ? s4.x : e == 1 ? s4.y : e == 2 ? s4.z : e == 3 ? s4.w
+                                                                                         : ~(SLOTF(X, ovf, si) + e - 4);
+                        X.sbuf[off + e - base] = v;
                     }
                 }
-                // next leader: lowest id not yet finished
-                int nl = L + 1;
-                while (nl < k) {
-                    const uint32_t w = ~done[nl >> 5] & (0xffffffffu << (nl & 31));
-                    if (w) { nl = (nl & ~31) + __ffs(w) - 1; break; }
-                    nl = (nl & ~31) + 32;
-                }
-                newL = nl < k ? nl : k;
-                if (newL < k) {
-                    if (ws.indeg[newL] != 0) err = RR_ERR_INTERNAL;
-                    Lg = load_geo(mv, newL);
-                    Lt = pst[PST_STRIDE * newL];
-                    int dd, rr, cc, rem; geo_at(Lg, Lt, &dd, &rr, &cc, &rem);
-                    line_remove(S, pst, newL, dd, rr, cc);
+                __syncwarp();
+                const int nb = min(SBUF, total - base);
+                for (int b0 = 0; b0 < nb; b0 += 32) {
+                    int ready = -1;
+                    int4 r = make_int4(0, 0, 0, 0), s4 = r;
+                    if (b0 + lane < nb) {
+                        int32_t e = X.sbuf[b0 + lane];
+                        if (e < 0) e = ws.succ[~e];
+                        const int id = e & SUCC_ID;
+                        // the record is fetched alongside the counter update
+                        r = ws.rec[id]; s4 = ws.succ4[id];
+                        if ((e & SUCC_SINGLE) || atomicSub(&ws.indeg[id], 1) == 1) ready = id;
+                    }
+                    const unsigned bal = __ballot_sync(FULL, ready >= 0);
+                    const int cnt = __popc(bal);
+                    if (cnt) {
+                        const int rank = __popc(bal & ((1u << lane) - 1u));
+                        // slots freed by finished members are recycled after this round
+                        const int ns_ = alloc_slot(X, rank, cnt, freeTop, ovfUsed, hi, k, &err);
+                        if (ready >= 0) fill_slot(X, ns_, ready, r, s4);
+                    }
+                    __syncwarp();
                 }
             }
+            // free the finished members' slots (shared-memory slots are recycled)
+            if (fin) {
+                const int id = SLOTF(X, id, si);
+                if (X.map[id & (MAPN - 1)] == si) X.map[id & (MAPN - 1)] = -1;
+                SLOTF(X, key, si) = 0;
+                SLOTF(X, id, si) = 0x7fffffff;
+            }
+            const bool recyc = fin && si < X.C;
+            const unsigned fb = __ballot_sync(FULL, recyc);
+            if (recyc) X.freeStk[freeTop + __popc(fb & ((1u << lane) - 1u))] = si;
+            freeTop += __popc(fb);
+            __syncwarp();
+        }
+        if (leaderDone && !err) {
+            // next leader: lowest id still held in a slot (usually L + 1)
+            int cand = -1;
+            const int nx = L + 1;
+            if (nx < k) {
+                const int si = X.map[nx & (MAPN - 1)];
+                if (si >= 0 && SLOTF(X, id, si) == nx) cand = si;
+            }
+            if (cand < 0) cand = lowest_slot(X, hi);
+            if (cand < 0) L = k;
+            else { Ls = cand; L = SLOTF(X, id, Ls); }
         }
         __syncwarp();
-        newL = __shfl_sync(FULL, newL, 0);
-        err = __shfl_sync(FULL, err, 0);
-        if (newL != L) {
-            L = newL;
-            if (L < k) {
-                Lg.sr = __shfl_sync(FULL, Lg.sr, 0); Lg.sc = __shfl_sync(FULL, Lg.sc, 0);
-                Lg.dr = __shfl_sync(FULL, Lg.dr, 0); Lg.dc = __shfl_sync(FULL, Lg.dc, 0);
-                Lg.len = __shfl_sync(FULL, Lg.len, 0); Lg.hl = __shfl_sync(FULL, Lg.hl, 0);
-            }
-        }
-        Lt = __shfl_sync(FULL, Lt, 0);
     }
     if (lane == 0) {
         I->n_ops = nop;

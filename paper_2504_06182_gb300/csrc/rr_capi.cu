@@ -21,7 +21,8 @@ __global__ void k_bsort(rr_instance *, JobWS *, int);
 __global__ void k_bsucc_count(rr_instance *, JobWS *, int);
 __global__ void k_bsucc_scan(rr_instance *, JobWS *, int, Arena);
 __global__ void k_bsucc_fill(rr_instance *, JobWS *, int);
-__global__ void k_sim(rr_instance *, JobWS *, int);
+__global__ void k_brec(rr_instance *, JobWS *, int);
+__global__ void k_sim(rr_instance *, JobWS *, int, int, int);
 }  // namespace rrk
 
 using namespace rrk;
@@ -183,10 +184,19 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
     k_bsucc_scan<<<count, 1024, 0, s>>>(d_inst, ctx->d_ws, count, A);
     mark(ctx, s, "k_bsucc_fill");
     k_bsucc_fill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
-    const int Wm = (max_side + 31) / 32;
-    const size_t simSmem = sizeof(int32_t) * (size_t)(8 * max_side + 4 * Wm + max_side + 2) + 64;
+    mark(ctx, s, "k_brec");
+    k_brec<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    // simulation: one warp per instance; ready-move slots, line lists and
+    // buffers in shared memory (layout mirrored in k_sim)
+    const int slotCap = 2 * max_side + 64, lineCap = max_side;
+    // s4 (16 B) + eight int32 fields + free stack per slot; staging; sort keys;
+    // id map; member list; successor buffer; new ids; two 64-word masks
+    const size_t simSmem = 16ull * slotCap + 16ull * 64 + 8ull * 2 * (lineCap + 2) + 4ull * 9 * slotCap +
+                           4ull * 1024 + 4ull * (lineCap + 2) + 4ull * 512 + 4ull * 32 + 4ull * 128 + 64;
+    if (simSmem > 227 * 1024) return fail(ctx, RR_ERR_ARG, "simulation shared memory %zu too large", simSmem);
+    CUDA_TRY(cudaFuncSetAttribute(k_sim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)simSmem));
     mark(ctx, s, "k_sim");
-    k_sim<<<count, 32, simSmem, s>>>(d_inst, ctx->d_ws, count);
+    k_sim<<<count, 32, simSmem, s>>>(d_inst, ctx->d_ws, count, slotCap, lineCap);
     mark(ctx, s, nullptr);
     CUDA_TRY(cudaGetLastError());
     return RR_OK;

@@ -76,10 +76,16 @@ struct JobWS {
     int32_t *succOff;      // k + 1
     int32_t *succ;         // E
     int32_t *indeg;        // k
-    int32_t *pst;          // k * PST_STRIDE simulation state
+    int4 *rec;             // k: packed geometry, successor count, overflow offset
+    int4 *succ4;           // k: first four successors (flagged, -1 padded)
+    int32_t *ready0;       // k + 1: moves without predecessors; [k] = their count
+    void *slotOvf;         // k simulation slots beyond the shared-memory ones
 };
 
-constexpr int PST_STRIDE = 5;  // t, rowPrev, rowNext, colPrev, colNext
+// Successor entries carry this flag when the successor has a single
+// predecessor: it becomes ready as soon as that predecessor finishes.
+constexpr int32_t SUCC_SINGLE = 1 << 30;
+constexpr int32_t SUCC_ID = SUCC_SINGLE - 1;
 
 __device__ __forceinline__ void *arena_alloc(const Arena &A, unsigned long long bytes, bool *ok)
 {
