@@ -343,16 +343,20 @@ __global__ void k_brec(rr_instance *inst, JobWS *wsv, int count)
 //
 // The ready moves live in a slot table (structure of arrays). Slots below
 // the shared-memory capacity are in shared memory, the rest in a global
-// overflow area with the same layout. Each batch is composed by one
-// warp-wide pass over the slot table: every lane tests its slots against the
-// leader's row and column for the leader's direction, giving both candidate
-// lines with their smallest ids, their members (as ballot masks), their
-// shortest remaining straight leg, and the distance to the nearest waiting
-// move of the same direction that the leader's line will reach.
+// overflow area with the same layout. Per-(direction, row) and
+// per-(direction, column) counters of ready moves (the leader included) tell
+// in O(1) whether the leader's row and column hold other moves of its
+// direction; if not, the leader moves alone until the next pickup, found in
+// bitmaps of non-empty rows (vertical directions) and columns (horizontal
+// ones). Otherwise one warp-wide pass over the slot table collects both
+// candidate lines (ballot compaction), their smallest ids, their shortest
+// remaining straight legs and the nearest waiting move the leader's line
+// will reach.
 
 constexpr int MAPN = 1024;      // id -> slot cache for finding the next leader
 constexpr int SBUF = 512;       // successor entries released per round
 constexpr int KEY_LIVE = 1 << 22;
+constexpr int INTMAX = 0x7fffffff;
 
 struct SlotSoA {
     int32_t *key;     // row | col << 10 | dir << 20 | KEY_LIVE; 0 when free
@@ -366,15 +370,14 @@ struct SlotSoA {
 
 struct Sim {
     SlotSoA sm, gm;
-    int C;
+    int C, m, n, Wm, Wn;
     int32_t *freeStk;
     int32_t *map;
+    int32_t *rowCnt, *colCnt;   // [4][m], [4][n]
+    uint32_t *rowBits, *colBits;  // [2][Wm] for directions 0, 1; [2][Wn] for 2, 3
+    long long *MkA, *MkB;       // candidate lines: id << 32 | slot
     int32_t *M;                 // member slots of the current batch, sorted by id
-    long long *Mk;              // sort keys (id << 32 | slot)
-    uint32_t *maskA, *maskB;    // ballot masks of the two candidate lines
     int32_t *sbuf;
-    int4 *stRec, *stS4;
-    int32_t *newIds;
 };
 
 #define SLOTF(X, f, i) (*((i) < (X).C ? &(X).sm.f[(i)] : &(X).gm.f[(i) - (X).C]))
@@ -398,11 +401,41 @@ __device__ __forceinline__ int warp_min(int v)
     return v;
 }
 
+// Add delta (+1 or -1) to the line counters of a live key and keep the
+// pickup bitmaps equal to "counter > 0". Within one warp step all updates
+// must have the same sign.
+__device__ __forceinline__ void cnt_add(const Sim &X, int key, int delta)
+{
+    const int r = key & 1023, c = (key >> 10) & 1023, d = (key >> 20) & 3;
+    const int o1 = atomicAdd(&X.rowCnt[d * X.m + r], delta);
+    const int o2 = atomicAdd(&X.colCnt[d * X.n + c], delta);
+    if (d < 2) {
+        if (delta > 0 && o1 == 0) atomicOr(&X.rowBits[d * X.Wm + (r >> 5)], 1u << (r & 31));
+        if (delta < 0 && o1 == 1) atomicAnd(&X.rowBits[d * X.Wm + (r >> 5)], ~(1u << (r & 31)));
+    } else {
+        if (delta > 0 && o2 == 0) atomicOr(&X.colBits[(d - 2) * X.Wn + (c >> 5)], 1u << (c & 31));
+        if (delta < 0 && o2 == 1) atomicAnd(&X.colBits[(d - 2) * X.Wn + (c >> 5)], ~(1u << (c & 31)));
+    }
+}
+
+// First i in 1..maxq with bit (pos + i*delta) set, or 0.
+__device__ int bit_scan(const uint32_t *b, int limit, int pos, int delta, int maxq)
+{
+    for (int i = 1; i <= maxq; ++i) {
+        const int x = pos + i * delta;
+        if (x < 0 || x >= limit) return 0;
+        const uint32_t w = b[x >> 5];
+        if (w == 0u) { i = delta > 0 ? ((x | 31) - pos) : (pos - (x & ~31)); continue; }
+        if ((w >> (x & 31)) & 1u) return i;
+    }
+    return 0;
+}
+
 // Lowest move id held in slots [0, hi) and its slot (warp-cooperative).
 __device__ int lowest_slot(const Sim &X, int hi)
 {
     const int lane = threadIdx.x & 31;
-    int best = 0x7fffffff, bs = -1;
+    int best = INTMAX, bs = -1;
     for (int i = lane; i < hi; i += 32) {
         const int id = SLOTF(X, id, i);
         if (id < best) { best = id; bs = i; }
@@ -412,13 +445,29 @@ __device__ int lowest_slot(const Sim &X, int hi)
         const int ob = __shfl_xor_sync(FULL, best, o), os = __shfl_xor_sync(FULL, bs, o);
         if (ob < best || (ob == best && os < bs)) { best = ob; bs = os; }
     }
-    return best == 0x7fffffff ? -1 : bs;
+    return best == INTMAX ? -1 : bs;
 }
 
-// Sort Mk[0..n) ascending (warp-cooperative bitonic sort in shared memory).
+// Sort a[0..n) ascending: registers for n <= 32, else a shared-memory
+// bitonic network (a must have room for the next power of two).
 __device__ void warp_sort64(long long *a, int n)
 {
     const int lane = threadIdx.x & 31;
+    if (n <= 32) {
+        long long v = lane < n ? a[lane] : 0x7fffffffffffffffll;
+#pragma unroll
+        for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                const long long o = __shfl_xor_sync(FULL, v, jj);
+                const bool up = (lane & kk) == 0, low = (lane & jj) == 0;
+                v = (low == up) ? (v < o ? v : o) : (v > o ? v : o);
+            }
+        }
+        if (lane < n) a[lane] = v;
+        __syncwarp();
+        return;
+    }
     int P = 1;
     while (P < n) P <<= 1;
     for (int i = n + lane; i < P; i += 32) a[i] = 0x7fffffffffffffffll;
@@ -438,8 +487,8 @@ __device__ void warp_sort64(long long *a, int n)
     }
 }
 
-// Allocate `cnt` slots (warp-cooperative); returns this lane's slot for
-// rank < cnt. freeTop / ovfUsed / hi are warp-uniform.
+// Allocate `cnt` slots (warp-cooperative); lane `rank` < cnt gets a slot.
+// freeTop / ovfUsed / hi are warp-uniform.
 __device__ __forceinline__ int alloc_slot(const Sim &X, int rank, int cnt, int &freeTop, int &ovfUsed, int &hi,
                                           int kmax, int *err)
 {
@@ -451,9 +500,8 @@ __device__ __forceinline__ int alloc_slot(const Sim &X, int rank, int cnt, int &
     ovfUsed += cnt - fromStack;
     if (ovfUsed > kmax) *err = RR_ERR_INTERNAL;
     int top = si + 1;
-    top = max(top, __shfl_xor_sync(FULL, top, 16)); top = max(top, __shfl_xor_sync(FULL, top, 8));
-    top = max(top, __shfl_xor_sync(FULL, top, 4)); top = max(top, __shfl_xor_sync(FULL, top, 2));
-    top = max(top, __shfl_xor_sync(FULL, top, 1));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) top = max(top, __shfl_xor_sync(FULL, top, o));
     hi = max(hi, top);
     return si;
 }
@@ -462,7 +510,8 @@ __device__ __forceinline__ void fill_slot(const Sim &X, int si, int id, int4 r, 
 {
     int rr, cc, d, rem, len;
     move_pos(r.x, r.y, 0, &rr, &cc, &d, &rem, &len);
-    SLOTF(X, key, si) = key_of(rr, cc, d);
+    const int key = key_of(rr, cc, d);
+    SLOTF(X, key, si) = key;
     SLOTF(X, id, si) = id;
     SLOTF(X, g0, si) = r.x;
     SLOTF(X, g1, si) = r.y;
@@ -472,6 +521,7 @@ __device__ __forceinline__ void fill_slot(const Sim &X, int si, int id, int4 r, 
     SLOTF(X, ovf, si) = r.w;
     SLOTF(X, s4, si) = s4;
     X.map[id & (MAPN - 1)] = si;
+    cnt_add(X, key, +1);
 }
 
 __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int lineCap)
@@ -483,17 +533,19 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
     if (!live(I)) return;
     JobWS &ws = wsv[q];
     const int k = (int)I->n_moves;
+    const int m = I->m, n = I->n;
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     if (k == 0) { if (lane == 0) { I->n_ops = 0; I->n_members = 0; } return; }
 
     // shared-memory layout (mirrored by the launcher's size computation)
     Sim X;
-    X.C = slotCap;
+    X.C = slotCap; X.m = m; X.n = n; X.Wm = (m + 31) >> 5; X.Wn = (n + 31) >> 5;
+    const int lbuf = 2 * (lineCap + 2);
     X.sm.s4 = smem_i4;
-    X.stRec = X.sm.s4 + slotCap;
-    X.stS4 = X.stRec + 32;
-    X.Mk = (long long *)(X.stS4 + 32);
-    int32_t *p32 = (int32_t *)(X.Mk + 2 * (lineCap + 2));
+    X.MkA = (long long *)(X.sm.s4 + slotCap);
+    X.MkB = X.MkA + lbuf;
+    int32_t *p32 = (int32_t *)(X.MkB + lbuf);
     X.sm.key = p32; p32 += slotCap;
     X.sm.id = p32; p32 += slotCap;
     X.sm.g0 = p32; p32 += slotCap;
@@ -506,11 +558,11 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
     X.map = p32; p32 += MAPN;
     X.M = p32; p32 += lineCap + 2;
     X.sbuf = p32; p32 += SBUF;
-    X.newIds = p32; p32 += 32;
-    X.maskA = (uint32_t *)p32; p32 += 64;
-    X.maskB = (uint32_t *)p32; p32 += 64;
-    // overflow slots (global), same structure
-    {
+    X.rowCnt = p32; p32 += 4 * lineCap;
+    X.colCnt = p32; p32 += 4 * lineCap;
+    X.rowBits = (uint32_t *)p32; p32 += 2 * ((lineCap + 31) >> 5);
+    X.colBits = (uint32_t *)p32;
+    {   // overflow slots (global), same structure
         char *g = (char *)ws.slotOvf;
         const size_t K1 = (size_t)k + 1;
         X.gm.s4 = (int4 *)g;               g += 16 * K1;
@@ -523,8 +575,12 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
         X.gm.nsucc = (int32_t *)g;         g += 4 * K1;
         X.gm.ovf = (int32_t *)g;
     }
-    for (int i = lane; i < slotCap; i += 32) { X.sm.key[i] = 0; X.sm.id[i] = 0x7fffffff; X.freeStk[i] = slotCap - 1 - i; }
+    for (int i = lane; i < slotCap; i += 32) { X.sm.key[i] = 0; X.sm.id[i] = INTMAX; X.freeStk[i] = slotCap - 1 - i; }
     for (int i = lane; i < MAPN; i += 32) X.map[i] = -1;
+    for (int i = lane; i < 4 * m; i += 32) X.rowCnt[i] = 0;
+    for (int i = lane; i < 4 * n; i += 32) X.colCnt[i] = 0;
+    for (int i = lane; i < 2 * X.Wm; i += 32) X.rowBits[i] = 0u;
+    for (int i = lane; i < 2 * X.Wn; i += 32) X.colBits[i] = 0u;
     int freeTop = slotCap, ovfUsed = 0, hi = 0, err = 0;
     __syncwarp();
 
@@ -554,114 +610,88 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
 
     while (!err && L < k) {
         if (++guard > guard_max) { err = RR_ERR_TIMEOUT; break; }
-        // leader state (uniform)
         int lr, lc, d, remL, lenL;
-        const int Lg0 = SLOTF(X, g0, Ls), Lg1 = SLOTF(X, g1, Ls), Lt = SLOTF(X, t, Ls);
-        move_pos(Lg0, Lg1, Lt, &lr, &lc, &d, &remL, &lenL);
+        move_pos(SLOTF(X, g0, Ls), SLOTF(X, g1, Ls), SLOTF(X, t, Ls), &lr, &lc, &d, &remL, &lenL);
         const int sgn = (d == 1 || d == 3) ? 1 : -1;
-        // one pass over the slot table (shared-memory part unrolled for
-        // memory-level parallelism, overflow part after it)
-        int minA = 0x7fffffff, minB = 0x7fffffff, pickA = 0x7fffffff, pickB = 0x7fffffff;
-        int remA = 0x7fffffff, remB = 0x7fffffff;
-        const int nwords = (hi + 31) >> 5;
-        auto visit = [&](int key, int i, int w) {
-            const bool same = (key & KEY_LIVE) && ((key >> 20) & 3) == d && i != Ls;
-            const int sr = key & 1023, sc = (key >> 10) & 1023;
-            const bool inA = same && sr == lr, inB = same && sc == lc;
-            if (inA || inB) {
-                const int id = SLOTF(X, id, i);
-                const int rem = SLOTF(X, legEnd, i) - SLOTF(X, t, i);
+        const int othersA = X.rowCnt[d * m + lr] - 1, othersB = X.colCnt[d * n + lc] - 1;
+        int kseg = remL, ns = 1;
+        long long *Mk = X.MkA;
+        if (othersA == 0 && othersB == 0) {
+            // the leader alone until the next waiting move of its direction
+            if (kseg > 1) {
+                const int hit = d >= 2 ? bit_scan(X.colBits + (d - 2) * X.Wn, n, lc, sgn, kseg - 1)
+                                       : bit_scan(X.rowBits + d * X.Wm, m, lr, sgn, kseg - 1);
+                if (hit > 0) kseg = hit;
+            }
+        } else {
+            int minA = INTMAX, minB = INTMAX, pickA = INTMAX, pickB = INTMAX, remA = INTMAX, remB = INTMAX;
+            int cntA = 0, cntB = 0;
+            auto visit = [&](int key, int id, int rem, int i) {
+                const bool same = (key & KEY_LIVE) && ((key >> 20) & 3) == d && i != Ls;
+                const int sr = key & 1023, sc = (key >> 10) & 1023;
+                const bool inA = same && sr == lr, inB = same && sc == lc;
                 if (inA) { minA = min(minA, id); remA = min(remA, rem); }
                 if (inB) { minB = min(minB, id); remB = min(remB, rem); }
-            }
-            if (same) {
                 const int dist = (d >= 2 ? sc - lc : sr - lr) * sgn;
-                if (dist > 0) {
+                if (same && dist > 0) {
                     if (!inA) pickA = min(pickA, dist);
                     if (!inB) pickB = min(pickB, dist);
                 }
-            }
-            const unsigned bA = __ballot_sync(FULL, inA), bB = __ballot_sync(FULL, inB);
-            if (lane == 0) { X.maskA[w] = bA; X.maskB[w] = bB; }
-        };
-        const int hs = min(hi, X.C);
-        const int wsm = (hs + 31) >> 5;
-        int w = 0;
-        for (; w + 4 <= wsm; w += 4) {
-            int kk[4];
+                const unsigned bA = __ballot_sync(FULL, inA), bB = __ballot_sync(FULL, inB);
+                const long long kv = ((long long)id << 32) | (unsigned)i;
+                if (inA && cntA + __popc(bA & lt) < lbuf) X.MkA[cntA + __popc(bA & lt)] = kv;
+                if (inB && cntB + __popc(bB & lt) < lbuf) X.MkB[cntB + __popc(bB & lt)] = kv;
+                cntA += __popc(bA);
+                cntB += __popc(bB);
+            };
+            const int hs = min(hi, X.C);
+            int i0 = 0;
+            for (; i0 + 128 <= hs; i0 += 128) {
+                int kk[4], id[4], le[4], tt[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) { const int i = 32 * (w + u) + lane; kk[u] = i < hs ? X.sm.key[i] : 0; }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) visit(kk[u], 32 * (w + u) + lane, w + u);
-        }
-        for (; w < nwords; ++w) {
-            const int i = 32 * w + lane;
-            visit(i < hi ? SLOTF(X, key, i) : 0, i, w);
-        }
-        minA = warp_min(minA); minB = warp_min(minB);
-        pickA = warp_min(pickA); pickB = warp_min(pickB);
-        remA = warp_min(remA); remB = warp_min(remB);
-        const bool any = minA != 0x7fffffff || minB != 0x7fffffff;
-        const bool useA = minA < minB;
-        int kseg = remL;
-        if (any) kseg = min(kseg, useA ? remA : remB);
-        kseg = min(kseg, useA || !any ? pickA : pickB);
-        __syncwarp();
-        // members: the leader, then the chosen line in ascending id
-        int ns = 1;
-        if (any) {
-            const uint32_t *mask = useA ? X.maskA : X.maskB;
-            int carry = 0;
-            for (int wb = 0; wb < nwords; wb += 32) {
-                const int w = wb + lane;
-                const uint32_t bits = w < nwords ? mask[w] : 0u;
-                const int c = __popc(bits);
-                const int incl = warp_incl_scan(c);
-                int pos = carry + incl - c;
-                uint32_t b = bits;
-                while (b) {
-                    const int i = 32 * w + __ffs(b) - 1;
-                    b &= b - 1;
-                    X.Mk[pos++] = ((long long)SLOTF(X, id, i) << 32) | (unsigned)i;
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + 32 * u + lane;
+                    kk[u] = X.sm.key[i]; id[u] = X.sm.id[i]; le[u] = X.sm.legEnd[i]; tt[u] = X.sm.t[i];
                 }
-                carry += __shfl_sync(FULL, incl, 31);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) visit(kk[u], id[u], le[u] - tt[u], i0 + 32 * u + lane);
             }
+            for (; i0 < hi; i0 += 32) {
+                const int i = i0 + lane;
+                const bool ok = i < hi;
+                const int key = ok ? SLOTF(X, key, i) : 0;
+                const int id = ok ? SLOTF(X, id, i) : INTMAX;
+                const int rem = ok ? SLOTF(X, legEnd, i) - SLOTF(X, t, i) : 0;
+                visit(key, id, rem, i);
+            }
+            minA = warp_min(minA); minB = warp_min(minB);
+            pickA = warp_min(pickA); pickB = warp_min(pickB);
+            remA = warp_min(remA); remB = warp_min(remB);
+            if (cntA > lineCap || cntB > lineCap) { err = RR_ERR_INTERNAL; break; }
+            const bool useA = minA < minB;
+            kseg = min(kseg, useA ? min(remA, pickA) : min(remB, pickB));
+            Mk = useA ? X.MkA : X.MkB;
+            const int cnt = useA ? cntA : cntB;
             __syncwarp();
-            if (carry > lineCap) { err = RR_ERR_INTERNAL; break; }
-            if (carry <= 32) {
-                // bitonic sort across the warp's registers
-                long long v = lane < carry ? X.Mk[lane] : 0x7fffffffffffffffll;
-#pragma unroll
-                for (int kk = 2; kk <= 32; kk <<= 1) {
-#pragma unroll
-                    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-                        const long long o = __shfl_xor_sync(FULL, v, jj);
-                        const bool up = (lane & kk) == 0, low = (lane & jj) == 0;
-                        v = (low == up) ? (v < o ? v : o) : (v > o ? v : o);
-                    }
-                }
-                if (lane < carry) { X.Mk[lane] = v; X.M[1 + lane] = (int)(v & 0xffffffff); }
-            } else {
-                warp_sort64(X.Mk, carry);
-                for (int u = lane; u < carry; u += 32) X.M[1 + u] = (int)(X.Mk[u] & 0xffffffff);
-            }
-            ns = 1 + carry;
+            warp_sort64(Mk, cnt);
+            for (int u = lane; u < cnt; u += 32) X.M[1 + u] = (int)(Mk[u] & 0xffffffff);
+            ns = 1 + cnt;
         }
         if (lane == 0) X.M[0] = Ls;
         __syncwarp();
         if (kseg < 1) { err = RR_ERR_INTERNAL; break; }
-        // kseg identical batches
+
+        // kseg identical batches: the leader, then the line in ascending id
         const int64_t addm = (int64_t)kseg * ns;
         if (!overflow && nop + kseg <= cap_ops && nmem + addm <= cap_mem) {
             for (int i = lane; i < kseg; i += 32) ops[nop + i] = rr_op{d, (int32_t)(nmem + (int64_t)i * ns), ns};
             if (ns == 1) {
                 for (int i = lane; i < kseg; i += 32) mem[nmem + i] = L;
             } else {
-                // member u of every batch: the leader, then the sorted line
                 int u = lane % ns;
                 const int step = 32 % ns;
                 for (int64_t i = lane; i < addm; i += 32) {
-                    mem[nmem + i] = u == 0 ? L : (int)(X.Mk[u - 1] >> 32);
+                    mem[nmem + i] = u == 0 ? L : (int)(Mk[u - 1] >> 32);
                     u += step;
                     if (u >= ns) u -= ns;
                 }
@@ -676,29 +706,36 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
         int leaderDone = 0;
         for (int u0 = 0; u0 < ns; u0 += 32) {
             const int u = u0 + lane;
-            bool fin = false;
-            int si = -1, nsu = 0;
-            if (u < ns) {
+            bool fin = false, act = u < ns;
+            int si = -1, nsu = 0, newKey = 0, newLeg = 0, t = 0;
+            if (act) {
                 si = X.M[u];
-                const int t = SLOTF(X, t, si) + kseg;
+                t = SLOTF(X, t, si) + kseg;
                 int r_, c_, d_, rem, len;
                 move_pos(SLOTF(X, g0, si), SLOTF(X, g1, si), t, &r_, &c_, &d_, &rem, &len);
-                SLOTF(X, t, si) = t;
-                if (t >= len) { fin = true; nsu = SLOTF(X, nsucc, si); }
-                else { SLOTF(X, key, si) = key_of(r_, c_, d_); SLOTF(X, legEnd, si) = t + rem; }
+                fin = t >= len;
+                newKey = key_of(r_, c_, d_);
+                newLeg = t + rem;
+                cnt_add(X, SLOTF(X, key, si), -1);
             }
-            if (__shfl_sync(FULL, (int)fin, 0) && u0 == 0) leaderDone = 1;
+            __syncwarp();
+            if (act) {
+                SLOTF(X, t, si) = t;
+                if (fin) nsu = SLOTF(X, nsucc, si);
+                else { SLOTF(X, key, si) = newKey; SLOTF(X, legEnd, si) = newLeg; cnt_add(X, newKey, +1); }
+            }
+            if (u0 == 0 && __shfl_sync(FULL, (int)fin, 0)) leaderDone = 1;
+            __syncwarp();
             // successor entries of the finished members, in rounds of SBUF
-            int off = warp_incl_scan(nsu) - nsu;
+            const int off = warp_incl_scan(nsu) - nsu;
             const int total = __shfl_sync(FULL, off + nsu, 31);
             for (int base = 0; base < total; base += SBUF) {
                 if (fin) {
-                    for (int e = max(0, base - off); e < nsu && off + e < base + SBUF; ++e) {
-                        const int4 s4 = SLOTF(X, s4, si);
-                        const int v = e == 0 ? s4.x : e == 1 ? s4.y : e == 2 ? s4.z : e == 3 ? s4.w
-                                                                                         : ~(SLOTF(X, ovf, si) + e - 4);
-                        X.sbuf[off + e - base] = v;
-                    }
+                    const int4 s4 = SLOTF(X, s4, si);
+                    const int ov = SLOTF(X, ovf, si);
+                    for (int e = max(0, base - off); e < nsu && off + e < base + SBUF; ++e)
+                        X.sbuf[off + e - base] = e == 0 ? s4.x : e == 1 ? s4.y : e == 2 ? s4.z : e == 3 ? s4.w
+                                                                                              : ~(ov + e - 4);
                 }
                 __syncwarp();
                 const int nb = min(SBUF, total - base);
@@ -709,31 +746,28 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
                         int32_t e = X.sbuf[b0 + lane];
                         if (e < 0) e = ws.succ[~e];
                         const int id = e & SUCC_ID;
-                        // the record is fetched alongside the counter update
-                        r = ws.rec[id]; s4 = ws.succ4[id];
+                        r = ws.rec[id]; s4 = ws.succ4[id];     // fetched with the counter update
                         if ((e & SUCC_SINGLE) || atomicSub(&ws.indeg[id], 1) == 1) ready = id;
                     }
                     const unsigned bal = __ballot_sync(FULL, ready >= 0);
                     const int cnt = __popc(bal);
                     if (cnt) {
-                        const int rank = __popc(bal & ((1u << lane) - 1u));
-                        // slots freed by finished members are recycled after this round
-                        const int ns_ = alloc_slot(X, rank, cnt, freeTop, ovfUsed, hi, k, &err);
+                        const int ns_ = alloc_slot(X, __popc(bal & lt), cnt, freeTop, ovfUsed, hi, k, &err);
                         if (ready >= 0) fill_slot(X, ns_, ready, r, s4);
                     }
                     __syncwarp();
                 }
             }
-            // free the finished members' slots (shared-memory slots are recycled)
+            // free the finished members' slots (shared-memory ones are recycled)
             if (fin) {
                 const int id = SLOTF(X, id, si);
                 if (X.map[id & (MAPN - 1)] == si) X.map[id & (MAPN - 1)] = -1;
                 SLOTF(X, key, si) = 0;
-                SLOTF(X, id, si) = 0x7fffffff;
+                SLOTF(X, id, si) = INTMAX;
             }
             const bool recyc = fin && si < X.C;
             const unsigned fb = __ballot_sync(FULL, recyc);
-            if (recyc) X.freeStk[freeTop + __popc(fb & ((1u << lane) - 1u))] = si;
+            if (recyc) X.freeStk[freeTop + __popc(fb & lt)] = si;
             freeTop += __popc(fb);
             __syncwarp();
         }

@@ -189,10 +189,12 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
     // simulation: one warp per instance; ready-move slots, line lists and
     // buffers in shared memory (layout mirrored in k_sim)
     const int slotCap = 2 * max_side + 64, lineCap = max_side;
-    // s4 (16 B) + eight int32 fields + free stack per slot; staging; sort keys;
-    // id map; member list; successor buffer; new ids; two 64-word masks
-    const size_t simSmem = 16ull * slotCap + 16ull * 64 + 8ull * 2 * (lineCap + 2) + 4ull * 9 * slotCap +
-                           4ull * 1024 + 4ull * (lineCap + 2) + 4ull * 512 + 4ull * 32 + 4ull * 128 + 64;
+    // per slot: s4 (16 B), eight int32 fields and a free-stack entry; two
+    // candidate-line buffers of 2 (lineCap + 2) int64; id map; member list;
+    // successor buffer; line counters [4][m] + [4][n]; pickup bitmaps
+    const size_t simSmem = 16ull * slotCap + 2ull * 8 * 2 * (lineCap + 2) + 4ull * 9 * slotCap + 4ull * 1024 +
+                           4ull * (lineCap + 2) + 4ull * 512 + 4ull * 8 * lineCap + 4ull * 4 * ((lineCap + 31) / 32) +
+                           64;
     if (simSmem > 227 * 1024) return fail(ctx, RR_ERR_ARG, "simulation shared memory %zu too large", simSmem);
     CUDA_TRY(cudaFuncSetAttribute(k_sim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)simSmem));
     mark(ctx, s, "k_sim");
