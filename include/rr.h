@@ -112,6 +112,26 @@ typedef struct {
 int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
                     cudaStream_t stream);
 
+/* rr_plan without allocation, for callers that must not allocate device
+ * memory: a real-time reconfiguration loop (cudaMalloc/cudaFree can
+ * synchronise the device and take unbounded time between imaging and the
+ * tweezer moves), code issuing work while a CUDA graph is being captured, or
+ * a plug-in whose device memory belongs to another allocator. The paper has
+ * no counterpart; the arguments, outputs and return codes are those of
+ * rr_plan, and no context is used.
+ * Workspace: a file-scope device array of RR_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library holds until exit. Grids above RR_NOALLOC_MAX_SIDE
+ * in either side are rejected with RR_ERR_ARG. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress): make that first
+ * call before any stream capture. All calls share the array and it keeps
+ * the last call's contents: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Synchronises `stream`. */
+#define RR_NOALLOC_MAX_SIDE 256
+#define RR_NOALLOC_SCRATCH_BYTES (512 * 1024)
+int rr_plan_noalloc(const void *d_grid, int layout, int m, int n, rr_rect rect,
+                    rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream);
+
 /* Stage tracing. With tracing on, every public call records a CUDA event on
  * its stream before each kernel and after the last one. rr_stage_times then
  * waits for those events and writes, for the most recent call, each kernel's

@@ -49,7 +49,8 @@ class rr_instance(ctypes.Structure):
 
 
 EXPORTS = ("rr_ctx_create", "rr_ctx_destroy", "rr_plan", "rr_batch", "rr_plan_batched", "rr_set_tracing",
-           "rr_stage_times", "rr_last_error")
+           "rr_stage_times", "rr_last_error", "rr_plan_noalloc")
+RR_NOALLOC_MAX_SIDE = 256
 
 _lib = None
 
@@ -77,6 +78,8 @@ def load(path: str = LIB_PATH):
     L.rr_set_tracing.restype = I32
     L.rr_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p), I32]
     L.rr_stage_times.restype = I32
+    L.rr_plan_noalloc.argtypes = [P, I32, I32, I32, rr_rect, P, I64, ctypes.POINTER(I64), P]
+    L.rr_plan_noalloc.restype = I32
     L.rr_last_error.argtypes = [P]
     L.rr_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -158,3 +161,12 @@ def rr_stage_times(ctx, cap: int = 32):
     if k < 0:
         raise RRError(k, rr_last_error(ctx))
     return [(names[i].decode(), float(ms[i])) for i in range(k)]
+
+
+def rr_plan_noalloc(d_grid, layout, m, n, rect, d_moves, cap, stream=None):
+    """rr_plan without a context or any allocation (sides up to
+    RR_NOALLOC_MAX_SIDE). Returns (status, n_moves)."""
+    nm = ctypes.c_int64(0)
+    st = load().rr_plan_noalloc(_addr(d_grid), int(layout), int(m), int(n), rr_rect(*[int(v) for v in rect]),
+                                _addr(d_moves), int(cap), ctypes.byref(nm), _stream(stream))
+    return st, nm.value
