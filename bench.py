@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-sample", type=int, default=96, help="grids run one per call for the plain baseline")
+    ap.add_argument("--served-requests", type=int, default=2000, help="requests of the served run (0: skip)")
+    ap.add_argument("--served-load", type=float, default=0.8, help="arrival rate as a fraction of saturation")
     return ap.parse_args()
 
 
@@ -139,6 +142,95 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ plain
+
+def run_plain(rr, P, insts, sample):
+    """One grid per call (rr_plan then rr_batch, each synchronising), the
+    plain single-instance GPU path, on the first `sample` grids."""
+    import torch
+    from paper_2504_06182_gb300.planner import Planner  # noqa: F401
+    grids = []
+    for inst in insts[:sample]:
+        w = gridgen.pack_bits32(inst.grid).view(np.int32)
+        grids.append((torch.from_numpy(np.ascontiguousarray(w)).cuda(), inst))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g, inst in grids:
+        s_ = inst.grid.shape[0]
+        st, mv = P.plan(g, inst.rect, layout=rr.RR_BITS32, n=s_, cap=2 * s_ * s_)
+        if st == rr.RR_OK and len(mv):
+            P.batch(mv, s_, s_)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    return {"value": len(grids) / secs, "unit": "grids/s",
+            "sample": f"first {len(grids)} grids of the workload, one rr_plan + rr_batch call each"}
+
+
+# ------------------------------------------------------------------ served
+
+SERVED_SIDES = gridgen.SIDES_SERVED
+
+
+def run_served(rr, requests, load, seed=5):
+    """Continuous batching: Poisson arrivals of grids with side uniform in
+    {64, 80, ..., 512}, p = 0.6, centred floor(0.7 side) target, submitted from
+    host memory; latency = completion - submission per request."""
+    pool = []
+    for g in range(min(256, requests)):
+        side, _ = gridgen.mixed_draw(seed, g, SERVED_SIDES, 0.6, 0.6)
+        inst = gridgen.square_instance(seed, g, side, 0.6)
+        pool.append((np.ascontiguousarray(gridgen.pack_bits32(inst.grid).view(np.int32)), inst))
+    srv = rr.rr_serve_open(max_side=512, slots=96, streams=4, max_wave=24, flags=rr.RR_WITH_BATCH,
+                           arena_bytes=6 << 30, heap_bytes=24 << 30)
+    try:
+        def submit(i):
+            w, inst = pool[i % len(pool)]
+            st, t = rr.rr_serve_submit(srv, w, rr.RR_BITS32, inst.grid.shape[0], inst.grid.shape[1], inst.rect)
+            if st != rr.RR_OK:
+                raise rr.RRError(st, "rr_serve_submit")
+            return t
+
+        def drain(tickets, lat, block):
+            keep = []
+            for t in tickets:
+                st, res = rr.rr_serve_poll(srv, t, 60_000_000 if block else 0)
+                if st == rr.RR_OK:
+                    if res.status not in (rr.RR_OK, rr.RR_INFEASIBLE):
+                        raise rr.RRError(res.status, "served request failed")
+                    lat.append(res.t_done_us - res.t_submit_us)
+                    rr.rr_serve_release(srv, t)
+                else:
+                    keep.append(t)
+            return keep
+
+        # saturation throughput: a burst of the pool's requests at once
+        nb = min(len(pool), 192)
+        t0 = time.perf_counter()
+        out = [submit(i) for i in range(nb)]
+        out = drain(out, [], True)
+        sat = nb / (time.perf_counter() - t0)
+        # Poisson arrivals at `load` x saturation
+        rate = load * sat
+        rng = np.random.default_rng(seed)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=requests))
+        lat, outstanding = [], []
+        t0 = time.perf_counter()
+        for i, ta in enumerate(arrivals):
+            while time.perf_counter() - t0 < ta:
+                outstanding = drain(outstanding, lat, False)
+            outstanding.append(submit(i))
+        while outstanding:
+            outstanding = drain(outstanding, lat, True)
+        secs = time.perf_counter() - t0
+        lat = np.array(lat) / 1e3
+        return {"requests": requests, "sides": "64..512 step 16", "p": 0.6, "rate_per_s": rate,
+                "saturation_grids_per_s": sat, "grids_per_s": requests / secs,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "note": f"requests cycle through {len(pool)} distinct seeded grids"}
+    finally:
+        rr.rr_serve_close(srv)
 
 
 # ------------------------------------------------------------------ ours
@@ -291,6 +383,12 @@ def run_ours(args, rank, world, local):
             torch.distributed.destroy_process_group()
         return
 
+    plain = run_plain(rr, P, insts, args.plain_sample) if args.plain_sample > 0 else None
+    del ops, mem, moves
+    P.close()
+    torch.cuda.empty_cache()
+    served = run_served(rr, args.served_requests, args.served_load) if args.served_requests > 0 else None
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -327,6 +425,8 @@ def run_ours(args, rank, world, local):
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "plain": plain,
+        "served": served,
         "clocks": clk,
         "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_tot.items(), key=lambda kv: -kv[1])},
         "totals_per_step": {"moves": int(tot_moves), "ops": int(tot_ops), "steps": int(tot_mem),

@@ -94,6 +94,7 @@ int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, int m, int n,
  * when it issued the work (no synchronisation); read the per-instance status
  * after synchronising the stream. */
 #define RR_WITH_BATCH 1
+#define RR_BATCH_ONLY 2   /* skip planning: instances carry moves and n_moves (status RR_OK) */
 typedef struct {
     const void *grid;
     int32_t layout, m, n, pad0;
@@ -105,12 +106,59 @@ typedef struct {
     int32_t status, pad1;                         /* output */
 } rr_instance;
 
-/* count in [1, 65535]; max_side bounds m and n of every instance (an
+/* With RR_BATCH_ONLY the planning kernels are skipped and each instance's
+ * moves[0 .. n_moves) are batched as by rr_batch (status must be RR_OK).
+ * count in [1, 65535]; max_side bounds m and n of every instance (an
  * instance above it gets RR_ERR_ARG); it sizes the launch shapes. The call
  * may grow the context's descriptor table (a synchronous cudaMalloc), so the
  * first call with a larger count must not be inside stream capture. */
 int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
                     cudaStream_t stream);
+
+/* ------------------------------------------------------------------ serving
+ * Continuous batching of planning requests (red-rec + batching per request):
+ * requests are admitted into preallocated device slots as they arrive and
+ * as slots free up, planned in waves (one rr_plan_batched call over the
+ * requests admitted since the previous wave) on a pool of streams so that
+ * waves overlap on the device, and, once a request's exact number of
+ * elementary steps is known, given result memory from a device heap and
+ * batched in a second wave (memory-based admission). A worker thread owned
+ * by the server drives the pipeline; the calling threads only submit, poll
+ * and release. Results stay on the device until released. */
+typedef struct rr_server rr_server;
+typedef struct {
+    int32_t max_side;        /* largest m or n accepted, <= RR_MAX_SIDE */
+    int32_t slots;           /* requests resident at once (device grid + move buffers) */
+    int32_t streams;         /* waves in flight at once */
+    int32_t max_wave;        /* requests per wave, <= slots */
+    int32_t flags;           /* RR_WITH_BATCH to also batch every plan */
+    int32_t pad;
+    int64_t arena_bytes;     /* workspace arena per stream */
+    int64_t heap_bytes;      /* device heap for batch results (16 B per elementary step) */
+} rr_serve_config;
+typedef struct {
+    int32_t status;          /* RR_OK, RR_INFEASIBLE or an error; RR_ERR_CAPACITY if the heap can never hold it */
+    int32_t m, n, pad;
+    int64_t n_moves, n_steps, n_ops, n_members;
+    const rr_move *d_moves;  /* device results, valid until rr_serve_release */
+    const rr_op *d_ops;
+    const int32_t *d_members;
+    double t_submit_us, t_admit_us, t_done_us;   /* host clock, microseconds since rr_serve_open */
+} rr_serve_result;
+/* Allocates every device buffer up front (slots, heap, arenas, descriptors). */
+int rr_serve_open(rr_server **srv, const rr_serve_config *cfg);
+/* Copies the grid (host memory, layouts as rr_plan) into the request queue
+ * and returns a ticket at once. RR_ERR_ARG for sizes above max_side. */
+int rr_serve_submit(rr_server *srv, const void *h_grid, int layout, int m, int n, rr_rect rect,
+                    int64_t *ticket);
+/* Waits up to timeout_us (0: just look) for the ticket: RR_OK and *out
+ * filled when done, RR_ERR_TIMEOUT otherwise, RR_ERR_ARG for an unknown
+ * ticket. */
+int rr_serve_poll(rr_server *srv, int64_t ticket, rr_serve_result *out, int64_t timeout_us);
+/* Frees the ticket's slot and result memory (its device pointers die). */
+int rr_serve_release(rr_server *srv, int64_t ticket);
+/* Stops the worker after in-flight waves finish and frees everything. */
+int rr_serve_close(rr_server *srv);
 
 /* rr_plan without allocation, for callers that must not allocate device
  * memory: a real-time reconfiguration loop (cudaMalloc/cudaFree can

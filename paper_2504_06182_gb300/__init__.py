@@ -19,6 +19,7 @@ RR_ERR_ARG, RR_ERR_CAPACITY, RR_ERR_CUDA = -1, -2, -3
 RR_ERR_TIMEOUT, RR_ERR_WORKSPACE, RR_ERR_INTERNAL = -4, -5, -6
 RR_U8, RR_BITS32 = 0, 1
 RR_WITH_BATCH = 1
+RR_BATCH_ONLY = 2
 RR_MAX_SIDE = 1024
 STATUS_NAMES = {0: "OK", 1: "INFEASIBLE", -1: "ERR_ARG", -2: "ERR_CAPACITY", -3: "ERR_CUDA",
                 -4: "ERR_TIMEOUT", -5: "ERR_WORKSPACE", -6: "ERR_INTERNAL"}
@@ -48,8 +49,23 @@ class rr_instance(ctypes.Structure):
                 ("status", ctypes.c_int32), ("pad1", ctypes.c_int32)]
 
 
+class rr_serve_config(ctypes.Structure):
+    _fields_ = [("max_side", ctypes.c_int32), ("slots", ctypes.c_int32), ("streams", ctypes.c_int32),
+                ("max_wave", ctypes.c_int32), ("flags", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("arena_bytes", ctypes.c_int64), ("heap_bytes", ctypes.c_int64)]
+
+
+class rr_serve_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("m", ctypes.c_int32), ("n", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("n_moves", ctypes.c_int64), ("n_steps", ctypes.c_int64), ("n_ops", ctypes.c_int64),
+                ("n_members", ctypes.c_int64), ("d_moves", ctypes.c_void_p), ("d_ops", ctypes.c_void_p),
+                ("d_members", ctypes.c_void_p), ("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double),
+                ("t_done_us", ctypes.c_double)]
+
+
 EXPORTS = ("rr_ctx_create", "rr_ctx_destroy", "rr_plan", "rr_batch", "rr_plan_batched", "rr_set_tracing",
-           "rr_stage_times", "rr_last_error", "rr_plan_noalloc")
+           "rr_stage_times", "rr_last_error", "rr_plan_noalloc", "rr_serve_open", "rr_serve_submit",
+           "rr_serve_poll", "rr_serve_release", "rr_serve_close")
 RR_NOALLOC_MAX_SIDE = 256
 
 _lib = None
@@ -80,6 +96,16 @@ def load(path: str = LIB_PATH):
     L.rr_stage_times.restype = I32
     L.rr_plan_noalloc.argtypes = [P, I32, I32, I32, rr_rect, P, I64, ctypes.POINTER(I64), P]
     L.rr_plan_noalloc.restype = I32
+    L.rr_serve_open.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(rr_serve_config)]
+    L.rr_serve_open.restype = I32
+    L.rr_serve_submit.argtypes = [P, P, I32, I32, I32, rr_rect, ctypes.POINTER(I64)]
+    L.rr_serve_submit.restype = I32
+    L.rr_serve_poll.argtypes = [P, I64, ctypes.POINTER(rr_serve_result), I64]
+    L.rr_serve_poll.restype = I32
+    L.rr_serve_release.argtypes = [P, I64]
+    L.rr_serve_release.restype = I32
+    L.rr_serve_close.argtypes = [P]
+    L.rr_serve_close.restype = I32
     L.rr_last_error.argtypes = [P]
     L.rr_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -170,3 +196,38 @@ def rr_plan_noalloc(d_grid, layout, m, n, rect, d_moves, cap, stream=None):
     st = load().rr_plan_noalloc(_addr(d_grid), int(layout), int(m), int(n), rr_rect(*[int(v) for v in rect]),
                                 _addr(d_moves), int(cap), ctypes.byref(nm), _stream(stream))
     return st, nm.value
+
+
+# ------------------------------------------------------------------ serving
+
+def rr_serve_open(max_side, slots, streams, max_wave, flags=RR_WITH_BATCH, arena_bytes=0, heap_bytes=1 << 30):
+    cfg = rr_serve_config(int(max_side), int(slots), int(streams), int(max_wave), int(flags), 0,
+                          int(arena_bytes), int(heap_bytes))
+    h = ctypes.c_void_p(0)
+    st = load().rr_serve_open(ctypes.byref(h), ctypes.byref(cfg))
+    if st != RR_OK:
+        raise RRError(st, "rr_serve_open failed")
+    return h.value
+
+
+def rr_serve_submit(srv, h_grid, layout, m, n, rect):
+    """h_grid: a contiguous numpy array in host memory. Returns (status, ticket)."""
+    t = ctypes.c_int64(0)
+    st = load().rr_serve_submit(srv, h_grid.ctypes.data_as(ctypes.c_void_p), int(layout), int(m), int(n),
+                                rr_rect(*[int(v) for v in rect]), ctypes.byref(t))
+    return st, t.value
+
+
+def rr_serve_poll(srv, ticket, timeout_us=0):
+    """Returns (status, rr_serve_result)."""
+    r = rr_serve_result()
+    st = load().rr_serve_poll(srv, int(ticket), ctypes.byref(r), int(timeout_us))
+    return st, r
+
+
+def rr_serve_release(srv, ticket) -> int:
+    return load().rr_serve_release(srv, int(ticket))
+
+
+def rr_serve_close(srv) -> int:
+    return load().rr_serve_close(srv)

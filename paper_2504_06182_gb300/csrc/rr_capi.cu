@@ -264,18 +264,23 @@ extern "C" int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int 
                                cudaStream_t stream)
 {
     if (!ctx || !d_inst || count < 1 || count > 65535 || max_side < 1 || max_side > RR_MAX_SIDE ||
-        (flags & ~RR_WITH_BATCH))
+        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY)))
         return fail(ctx, RR_ERR_ARG, "rr_plan_batched: bad argument (count=%d max_side=%d flags=%d)", count,
                     max_side, flags);
     int st = ensure_ws(ctx, count);
     if (st != RR_OK) return st;
     ctx->nmarks = 0;
     CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
+    if (flags & RR_BATCH_ONLY) return launch_batch(ctx, d_inst, count, max_side, stream);
     st = launch_plan(ctx, d_inst, count, max_side, stream);
     if (st != RR_OK) return st;
     if (flags & RR_WITH_BATCH) st = launch_batch(ctx, d_inst, count, max_side, stream);
     return st;
 }
+
+// Library-internal: size a context's descriptor table for `count` instances
+// up front (the server does this before any wave so that no call allocates).
+int rr_internal_reserve(rr_ctx *ctx, int count) { return ensure_ws(ctx, count); }
 
 extern "C" int rr_set_tracing(rr_ctx *ctx, int enable)
 {

@@ -158,3 +158,6 @@ __device__ __forceinline__ void set_status(rr_instance *I, int st)
 }
 
 } // namespace rrk
+
+// Library-internal hook between translation units (not part of the C ABI).
+int rr_internal_reserve(rr_ctx *ctx, int count);

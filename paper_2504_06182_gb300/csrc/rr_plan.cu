@@ -59,6 +59,15 @@ __device__ __forceinline__ int pool_bot_row(const ColInfo &D, const int16_t *row
 
 __device__ __forceinline__ bool live(const rr_instance *I) { return I->status == RR_OK; }
 
+// Adds a warp's elementary-step count to the instance total (every lane of
+// the warp calls it).
+__device__ __forceinline__ void add_steps(rr_instance *I, long long v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long *)&I->n_steps, (unsigned long long)v);
+}
+
 // ------------------------------------------------------------ validation
 
 __global__ void k_plan_setup(rr_instance *inst, JobWS *wsv, int count, int max_side, Arena A)
@@ -438,7 +447,7 @@ __global__ void k_emit_cols(rr_instance *inst, JobWS *wsv, int count)
 {
     const int q = blockIdx.y;
     if (q >= count) return;
-    const rr_instance *I = &inst[q];
+    rr_instance *I = &inst[q];
     if (!live(I)) return;
     JobWS &ws = wsv[q];
     const int m = I->m, n = I->n;
@@ -446,6 +455,7 @@ __global__ void k_emit_cols(rr_instance *inst, JobWS *wsv, int count)
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * (blockDim.x >> 5);
     rr_move *out = I->moves;
+    long long steps = 0;
     for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n; c += nw) {
         const ColInfo ci = ws.col[c];
         if (ci.nmoves == 0) continue;
@@ -460,15 +470,21 @@ __global__ void k_emit_cols(rr_instance *inst, JobWS *wsv, int count)
                 else if (k >= ci.ku_start) pos = ci.kd_end + (k - ci.ku_start);  // toward smaller rows
                 else continue;                                                // isolated
                 o[pos] = rr_move{s, c, r0 + k, c};
+                steps += iabs(r0 + k - s);
             }
         } else {   // KIND_OUTER_FULL
             const int nbg = m - r1, ndown = nbg - ci.botRun;
-            for (int k = lane; k < ndown; k += 32)
+            for (int k = lane; k < ndown; k += 32) {
                 o[ndown - 1 - k] = rr_move{rows[ci.K - nbg + k], c, r1 + k, c};
-            for (int k = ci.topRun + lane; k < r0; k += 32)
+                steps += r1 + k - rows[ci.K - nbg + k];
+            }
+            for (int k = ci.topRun + lane; k < r0; k += 32) {
                 o[ndown + (k - ci.topRun)] = rr_move{rows[k], c, k, c};
+                steps += rows[k] - k;
+            }
         }
     }
+    add_steps(I, steps);
 }
 
 // ---------------------------------------------------- S5/S6: receiver units
@@ -503,6 +519,7 @@ __global__ void k_emit_recv(rr_instance *inst, JobWS *wsv, int count)
     JobWS &ws = wsv[q];
     const int m = I->m, n = I->n;
     const int r0 = I->rect.r0, r1 = I->rect.r1, h = r1 - r0;
+    long long steps = 0;
     for (int r = blockIdx.x; r < ws.nrecv; r += gridDim.x) {
         const RecvInfo ri = ws.recv[r];
         const int j = ri.j;
@@ -528,7 +545,7 @@ __global__ void k_emit_recv(rr_instance *inst, JobWS *wsv, int count)
             s_nc = nc;
         }
         __syncthreads();
-        if (!live(I)) return;
+        if (!live(I)) break;
         const int nc = s_nc;
         rr_move *o = I->moves + ws.unitOff[n + r];
         const int ownTop = Rj.ntop, ownBand = Rj.nband;
@@ -615,8 +632,10 @@ __global__ void k_emit_recv(rr_instance *inst, JobWS *wsv, int count)
             else continue;                                 // isolated own band atom
             if (pos >= ri.nmoves) { set_status(I, RR_ERR_INTERNAL); continue; }
             o[pos] = rr_move{row, col, r0 + k, j};
+            steps += iabs(r0 + k - row) + iabs(j - col);
         }
     }
+    add_steps(I, steps);
 }
 
 } // namespace rrk

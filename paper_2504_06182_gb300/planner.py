@@ -95,3 +95,21 @@ def plan_batched(planner: Planner, inst_tensor: torch.Tensor, count: int, max_si
     st = rr_plan_batched(planner.ctx, inst_tensor, count, max_side, RR_WITH_BATCH if with_batch else 0, stream)
     if st != RR_OK:
         raise RRError(st, rr_last_error(planner.ctx))
+
+
+class _DeviceArray:
+    """Exposes a raw device address to torch through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3}
+
+
+def device_view(ptr: int, shape, dtype=torch.int32) -> torch.Tensor:
+    """Zero-copy torch view of device memory owned by the library (for
+    example a served request's results; valid until the request is
+    released)."""
+    typestr = {torch.int32: "<i4", torch.uint8: "|u1"}[dtype]
+    if not ptr or any(int(d) == 0 for d in shape):
+        return torch.empty(tuple(int(d) for d in shape), dtype=dtype, device="cuda")
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")
