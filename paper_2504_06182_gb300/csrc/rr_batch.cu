@@ -124,8 +124,8 @@ __global__ void k_bsetup(rr_instance *inst, JobWS *wsv, int count, Arena A)
             ws.nextAt = (int32_t *)arena_alloc(A, 4ull * (tp + 1), &ok);
             ws.succOff = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
             ws.indeg = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
-            ws.rec = (int4 *)arena_alloc(A, 16ull * (k + 1), &ok);
-            ws.succ4 = (int4 *)arena_alloc(A, 16ull * (k + 1), &ok);
+            ws.rec = (int4 *)arena_alloc(A, 32ull * (k + 1), &ok);   // record, successors: one 32 B sector
+            ws.succ4 = ws.rec + 1;
             ws.ready0 = (int32_t *)arena_alloc(A, 4ull * (k + 1) + 16, &ok);
             ws.slotOvf = arena_alloc(A, 64ull * (k + 1), &ok);
             ws.succ = nullptr; ws.E = 0;
@@ -333,56 +333,65 @@ __global__ void k_brec(rr_instance *inst, JobWS *wsv, int count)
             const int32_t f = sId | (ws.indeg[sId] == 1 ? SUCC_SINGLE : 0);
             if (e - lo < 4) v[e - lo] = f; else ws.succ[e] = f;
         }
-        ws.rec[b] = r;
-        ws.succ4[b] = make_int4(v[0], v[1], v[2], v[3]);
+        ws.rec[2 * b] = r;
+        ws.rec[2 * b + 1] = make_int4(v[0], v[1], v[2], v[3]);
         if (ws.indeg[b] == 0) ws.ready0[atomicAdd(&ws.ready0[k], 1)] = (int32_t)b;
     }
 }
 
 // ---------------------------------------------------------- simulation
 //
-// The ready moves live in a slot table (structure of arrays). Slots below
-// the shared-memory capacity are in shared memory, the rest in a global
-// overflow area with the same layout. Per-(direction, row) and
-// per-(direction, column) counters of ready moves (the leader included) tell
-// in O(1) whether the leader's row and column hold other moves of its
-// direction; if not, the leader moves alone until the next pickup, found in
-// bitmaps of non-empty rows (vertical directions) and columns (horizontal
-// ones). Otherwise one warp-wide pass over the slot table collects both
-// candidate lines (ballot compaction), their smallest ids, their shortest
-// remaining straight legs and the nearest waiting move the leader's line
-// will reach.
+// The ready moves live in a slot table (structure of arrays; shared memory
+// up to its capacity, then a global overflow area with the same layout).
+// The moves of the current batch other than the leader ("members") are kept
+// in a persistent array sorted by id; every other ready move ("static") is
+// linked into two lists, one per (direction, row) and one per (direction,
+// column), and flagged in per-direction bitmaps of non-empty rows (vertical
+// directions) or columns (horizontal ones) for pickup detection.
+//
+// Members always share one line (a row or a column) and one direction. At a
+// segment boundary the candidates of the leader's row are the statics of that
+// row list plus the members if they form that row (likewise for its column);
+// so a segment walks two lists, usually short, and merges the newcomers. The
+// batch is dissolved back into the lists only when the leader's line or
+// direction no longer matches the members'.
 
-constexpr int MAPN = 1024;      // id -> slot cache for finding the next leader
+constexpr int MAPN = 512;       // id -> slot cache for finding the next leader
 constexpr int SBUF = 512;       // successor entries released per round
 constexpr int KEY_LIVE = 1 << 22;
+constexpr int KEY_MEM = 1 << 23;
 constexpr int INTMAX = 0x7fffffff;
 
 struct SlotSoA {
-    int32_t *key;     // row | col << 10 | dir << 20 | KEY_LIVE; 0 when free
+    int32_t *key;     // row | col << 10 | dir << 20 | KEY_LIVE [| KEY_MEM]; 0 when free
     int32_t *id;      // move id, INT_MAX when free
     int32_t *g0, *g1; // src_row | src_col << 16, dst_row | dst_col << 16
-    int32_t *t;       // elementary steps done
-    int32_t *legEnd;  // t at the end of the current straight leg
-    int32_t *nsucc, *ovf;
+    int16_t *t;       // elementary steps done (paths are shorter than 2 048 steps)
+    int16_t *legEnd;  // t at the end of the current straight leg
+    int16_t *nsucc;
+    int32_t *ovf;
+    int32_t *rp, *rn, *cp, *cn;   // static-list links (slot indices, -1)
     int4 *s4;         // first four successors
 };
 
 struct Sim {
     SlotSoA sm, gm;
     int C, m, n, Wm, Wn;
-    int32_t *freeStk;
+    int16_t *freeStk;
     int32_t *map;
-    int32_t *rowCnt, *colCnt;   // [4][m], [4][n]
-    uint32_t *rowBits, *colBits;  // [2][Wm] for directions 0, 1; [2][Wn] for 2, 3
-    long long *MkA, *MkB;       // candidate lines: id << 32 | slot
-    int32_t *M;                 // member slots of the current batch, sorted by id
+    int32_t *rowHead, *colHead;     // [4][m], [4][n] static lists
+    uint32_t *rowBits, *colBits;    // [2][Wm] (dirs 0, 1), [2][Wn] (dirs 2, 3)
+    int32_t *Mid, *Msl;             // members sorted by id
+    long long *Kb;                  // sort / merge buffer
     int32_t *sbuf;
 };
 
 #define SLOTF(X, f, i) (*((i) < (X).C ? &(X).sm.f[(i)] : &(X).gm.f[(i) - (X).C]))
 
 __device__ __forceinline__ int key_of(int r, int c, int d) { return r | (c << 10) | (d << 20) | KEY_LIVE; }
+__device__ __forceinline__ int key_r(int k) { return k & 1023; }
+__device__ __forceinline__ int key_c(int k) { return (k >> 10) & 1023; }
+__device__ __forceinline__ int key_d(int k) { return (k >> 20) & 3; }
 
 // Position, direction and remaining straight leg after t steps of a move.
 __device__ __forceinline__ void move_pos(int g0, int g1, int t, int *r, int *c, int *d, int *rem, int *len)
@@ -401,21 +410,46 @@ __device__ __forceinline__ int warp_min(int v)
     return v;
 }
 
-// Add delta (+1 or -1) to the line counters of a live key and keep the
-// pickup bitmaps equal to "counter > 0". Within one warp step all updates
-// must have the same sign.
-__device__ __forceinline__ void cnt_add(const Sim &X, int key, int delta)
+__device__ __forceinline__ void bits_set(const Sim &X, int d, int r, int c)
 {
-    const int r = key & 1023, c = (key >> 10) & 1023, d = (key >> 20) & 3;
-    const int o1 = atomicAdd(&X.rowCnt[d * X.m + r], delta);
-    const int o2 = atomicAdd(&X.colCnt[d * X.n + c], delta);
-    if (d < 2) {
-        if (delta > 0 && o1 == 0) atomicOr(&X.rowBits[d * X.Wm + (r >> 5)], 1u << (r & 31));
-        if (delta < 0 && o1 == 1) atomicAnd(&X.rowBits[d * X.Wm + (r >> 5)], ~(1u << (r & 31)));
-    } else {
-        if (delta > 0 && o2 == 0) atomicOr(&X.colBits[(d - 2) * X.Wn + (c >> 5)], 1u << (c & 31));
-        if (delta < 0 && o2 == 1) atomicAnd(&X.colBits[(d - 2) * X.Wn + (c >> 5)], ~(1u << (c & 31)));
-    }
+    if (d < 2) atomicOr(&X.rowBits[d * X.Wm + (r >> 5)], 1u << (r & 31));
+    else atomicOr(&X.colBits[(d - 2) * X.Wn + (c >> 5)], 1u << (c & 31));
+}
+
+// Static-list maintenance. push/remove touch the row list and the column
+// list of the slot's current key; callers that run them on several lanes at
+// once must guarantee distinct lists (see dissolve()).
+__device__ void push_row(const Sim &X, int si, int key)
+{
+    int32_t *h = &X.rowHead[key_d(key) * X.m + key_r(key)];
+    SLOTF(X, rp, si) = -1; SLOTF(X, rn, si) = *h;
+    if (*h >= 0) SLOTF(X, rp, *h) = si;
+    *h = si;
+    if (key_d(key) < 2) atomicOr(&X.rowBits[key_d(key) * X.Wm + (key_r(key) >> 5)], 1u << (key_r(key) & 31));
+}
+__device__ void push_col(const Sim &X, int si, int key)
+{
+    int32_t *h = &X.colHead[key_d(key) * X.n + key_c(key)];
+    SLOTF(X, cp, si) = -1; SLOTF(X, cn, si) = *h;
+    if (*h >= 0) SLOTF(X, cp, *h) = si;
+    *h = si;
+    if (key_d(key) >= 2) atomicOr(&X.colBits[(key_d(key) - 2) * X.Wn + (key_c(key) >> 5)], 1u << (key_c(key) & 31));
+}
+__device__ void unlink_row(const Sim &X, int si, int key)
+{
+    const int p = SLOTF(X, rp, si), q = SLOTF(X, rn, si);
+    int32_t *h = &X.rowHead[key_d(key) * X.m + key_r(key)];
+    if (p >= 0) SLOTF(X, rn, p) = q; else *h = q;
+    if (q >= 0) SLOTF(X, rp, q) = p;
+    if (*h < 0 && key_d(key) < 2) atomicAnd(&X.rowBits[key_d(key) * X.Wm + (key_r(key) >> 5)], ~(1u << (key_r(key) & 31)));
+}
+__device__ void unlink_col(const Sim &X, int si, int key)
+{
+    const int p = SLOTF(X, cp, si), q = SLOTF(X, cn, si);
+    int32_t *h = &X.colHead[key_d(key) * X.n + key_c(key)];
+    if (p >= 0) SLOTF(X, cn, p) = q; else *h = q;
+    if (q >= 0) SLOTF(X, cp, q) = p;
+    if (*h < 0 && key_d(key) >= 2) atomicAnd(&X.colBits[(key_d(key) - 2) * X.Wn + (key_c(key) >> 5)], ~(1u << (key_c(key) & 31)));
 }
 
 // First i in 1..maxq with bit (pos + i*delta) set, or 0.
@@ -453,6 +487,7 @@ __device__ int lowest_slot(const Sim &X, int hi)
 __device__ void warp_sort64(long long *a, int n)
 {
     const int lane = threadIdx.x & 31;
+    if (n <= 1) return;
     if (n <= 32) {
         long long v = lane < n ? a[lane] : 0x7fffffffffffffffll;
 #pragma unroll
@@ -506,7 +541,8 @@ __device__ __forceinline__ int alloc_slot(const Sim &X, int rank, int cnt, int &
     return si;
 }
 
-__device__ __forceinline__ void fill_slot(const Sim &X, int si, int id, int4 r, int4 s4)
+// A newly ready move: fill its slot (the caller links it into the lists).
+__device__ __forceinline__ int fill_slot(const Sim &X, int si, int id, int4 r, int4 s4)
 {
     int rr, cc, d, rem, len;
     move_pos(r.x, r.y, 0, &rr, &cc, &d, &rem, &len);
@@ -516,18 +552,76 @@ __device__ __forceinline__ void fill_slot(const Sim &X, int si, int id, int4 r, 
     SLOTF(X, g0, si) = r.x;
     SLOTF(X, g1, si) = r.y;
     SLOTF(X, t, si) = 0;
-    SLOTF(X, legEnd, si) = rem;
-    SLOTF(X, nsucc, si) = r.z;
+    SLOTF(X, legEnd, si) = (int16_t)rem;
+    SLOTF(X, nsucc, si) = (int16_t)r.z;
     SLOTF(X, ovf, si) = r.w;
     SLOTF(X, s4, si) = s4;
     X.map[id & (MAPN - 1)] = si;
-    cnt_add(X, key, +1);
+    return key;
 }
 
-__global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int lineCap)
+// Pull the records of a move's first successors toward L1: they are read when
+// the move finishes, a few batches later.
+__device__ __forceinline__ void prefetch_succ(const JobWS &ws, int4 s4, int nsucc)
+{
+    const int v[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (e < nsucc) {
+            const int4 *a = ws.rec + 2 * (v[e] & SUCC_ID);
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+        }
+}
+
+// Turn the members back into statics (warp-cooperative). Members share one
+// line, so their perpendicular lists are distinct and are pushed in
+// parallel; the shared line list gets the members as one spliced chain.
+__device__ void dissolve(const Sim &X, int nm, bool rowLine)
+{
+    const int lane = threadIdx.x & 31;
+    if (nm <= 0) return;
+    const int k0 = SLOTF(X, key, X.Msl[0]) & ~KEY_MEM;
+    int32_t *lineHead = rowLine ? &X.rowHead[key_d(k0) * X.m + key_r(k0)] : &X.colHead[key_d(k0) * X.n + key_c(k0)];
+    const int oldHead = *lineHead;
+    __syncwarp();
+    for (int u = lane; u < nm; u += 32) {
+        const int si = X.Msl[u];
+        const int key = SLOTF(X, key, si) & ~KEY_MEM;
+        SLOTF(X, key, si) = key;
+        const int prv = u == 0 ? -1 : X.Msl[u - 1], nxt = u == nm - 1 ? oldHead : X.Msl[u + 1];
+        if (rowLine) { SLOTF(X, rp, si) = prv; SLOTF(X, rn, si) = nxt; push_col(X, si, key); }
+        else { SLOTF(X, cp, si) = prv; SLOTF(X, cn, si) = nxt; push_row(X, si, key); }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        if (oldHead >= 0) { if (rowLine) SLOTF(X, rp, oldHead) = X.Msl[nm - 1]; else SLOTF(X, cp, oldHead) = X.Msl[nm - 1]; }
+        *lineHead = X.Msl[0];
+        bits_set(X, key_d(k0), key_r(k0), key_c(k0));
+    }
+    __syncwarp();
+}
+
+// Instances grouped by size class (largest side <= classSide[c]) so that each
+// class's simulation launch gets shared memory sized for its own grids.
+__global__ void k_classify(rr_instance *inst, int count, int nclass, const int *classSide, int *classCount,
+                           int *classList)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+        const rr_instance *I = &inst[q];
+        if (!live(I)) continue;
+        const int side = max(I->m, I->n);
+        int c = 0;
+        while (c < nclass - 1 && side > classSide[c]) ++c;
+        classList[c * count + atomicAdd(&classCount[c], 1)] = q;
+    }
+}
+
+__global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, const int *classList, const int *classCount,
+                      int slotCap, int lineCap)
 {
     extern __shared__ int4 smem_i4[];
-    const int q = blockIdx.x;
+    if ((int)blockIdx.x >= *classCount) return;
+    const int q = classList[blockIdx.x];
     if (q >= count) return;
     rr_instance *I = &inst[q];
     if (!live(I)) return;
@@ -543,57 +637,65 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
     X.C = slotCap; X.m = m; X.n = n; X.Wm = (m + 31) >> 5; X.Wn = (n + 31) >> 5;
     const int lbuf = 2 * (lineCap + 2);
     X.sm.s4 = smem_i4;
-    X.MkA = (long long *)(X.sm.s4 + slotCap);
-    X.MkB = X.MkA + lbuf;
-    int32_t *p32 = (int32_t *)(X.MkB + lbuf);
+    X.Kb = (long long *)(X.sm.s4 + slotCap);
+    int32_t *p32 = (int32_t *)(X.Kb + lbuf);
     X.sm.key = p32; p32 += slotCap;
     X.sm.id = p32; p32 += slotCap;
     X.sm.g0 = p32; p32 += slotCap;
     X.sm.g1 = p32; p32 += slotCap;
-    X.sm.t = p32; p32 += slotCap;
-    X.sm.legEnd = p32; p32 += slotCap;
-    X.sm.nsucc = p32; p32 += slotCap;
     X.sm.ovf = p32; p32 += slotCap;
-    X.freeStk = p32; p32 += slotCap;
+    X.sm.rp = p32; p32 += slotCap;
+    X.sm.rn = p32; p32 += slotCap;
+    X.sm.cp = p32; p32 += slotCap;
+    X.sm.cn = p32; p32 += slotCap;
     X.map = p32; p32 += MAPN;
-    X.M = p32; p32 += lineCap + 2;
+    X.Mid = p32; p32 += lineCap + 2;
+    X.Msl = p32; p32 += lineCap + 2;
     X.sbuf = p32; p32 += SBUF;
-    X.rowCnt = p32; p32 += 4 * lineCap;
-    X.colCnt = p32; p32 += 4 * lineCap;
+    X.rowHead = p32; p32 += 4 * lineCap;
+    X.colHead = p32; p32 += 4 * lineCap;
     X.rowBits = (uint32_t *)p32; p32 += 2 * ((lineCap + 31) >> 5);
-    X.colBits = (uint32_t *)p32;
+    X.colBits = (uint32_t *)p32; p32 += 2 * ((lineCap + 31) >> 5);
+    int16_t *p16 = (int16_t *)p32;
+    X.sm.t = p16; p16 += slotCap;
+    X.sm.legEnd = p16; p16 += slotCap;
+    X.sm.nsucc = p16; p16 += slotCap;
+    X.freeStk = p16;
     {   // overflow slots (global), same structure
         char *g = (char *)ws.slotOvf;
         const size_t K1 = (size_t)k + 1;
         X.gm.s4 = (int4 *)g;               g += 16 * K1;
-        X.gm.key = (int32_t *)g;           g += 4 * K1;
-        X.gm.id = (int32_t *)g;            g += 4 * K1;
-        X.gm.g0 = (int32_t *)g;            g += 4 * K1;
-        X.gm.g1 = (int32_t *)g;            g += 4 * K1;
-        X.gm.t = (int32_t *)g;             g += 4 * K1;
-        X.gm.legEnd = (int32_t *)g;        g += 4 * K1;
-        X.gm.nsucc = (int32_t *)g;         g += 4 * K1;
-        X.gm.ovf = (int32_t *)g;
+        int32_t **f[9] = {&X.gm.key, &X.gm.id, &X.gm.g0, &X.gm.g1, &X.gm.ovf, &X.gm.rp, &X.gm.rn, &X.gm.cp, &X.gm.cn};
+        for (int u = 0; u < 9; ++u) { *f[u] = (int32_t *)g; g += 4 * K1; }
+        X.gm.t = (int16_t *)g;             g += 2 * K1;
+        X.gm.legEnd = (int16_t *)g;        g += 2 * K1;
+        X.gm.nsucc = (int16_t *)g;
     }
-    for (int i = lane; i < slotCap; i += 32) { X.sm.key[i] = 0; X.sm.id[i] = INTMAX; X.freeStk[i] = slotCap - 1 - i; }
+    for (int i = lane; i < slotCap; i += 32) { X.sm.key[i] = 0; X.sm.id[i] = INTMAX; X.freeStk[i] = (int16_t)(slotCap - 1 - i); }
     for (int i = lane; i < MAPN; i += 32) X.map[i] = -1;
-    for (int i = lane; i < 4 * m; i += 32) X.rowCnt[i] = 0;
-    for (int i = lane; i < 4 * n; i += 32) X.colCnt[i] = 0;
+    for (int i = lane; i < 4 * m; i += 32) X.rowHead[i] = -1;
+    for (int i = lane; i < 4 * n; i += 32) X.colHead[i] = -1;
     for (int i = lane; i < 2 * X.Wm; i += 32) X.rowBits[i] = 0u;
     for (int i = lane; i < 2 * X.Wn; i += 32) X.colBits[i] = 0u;
     int freeTop = slotCap, ovfUsed = 0, hi = 0, err = 0;
     __syncwarp();
 
-    // moves without predecessors
+    // moves without predecessors become statics
     const int32_t *ready0 = ws.ready0;
     const int nready0 = ready0[k];
     for (int base = 0; base < nready0; base += 32) {
         const int cnt = min(32, nready0 - base);
         int id = -1;
         int4 r = make_int4(0, 0, 0, 0), s4 = r;
-        if (lane < cnt) { id = ready0[base + lane]; r = ws.rec[id]; s4 = ws.succ4[id]; }
+        if (lane < cnt) { id = ready0[base + lane]; r = ws.rec[2 * id]; s4 = ws.rec[2 * id + 1]; }
         const int si = alloc_slot(X, lane, cnt, freeTop, ovfUsed, hi, k, &err);
-        if (lane < cnt) fill_slot(X, si, id, r, s4);
+        int key = 0;
+        if (lane < cnt) key = fill_slot(X, si, id, r, s4);
+        __syncwarp();
+        for (int u = 0; u < cnt; ++u) {
+            const int su = __shfl_sync(FULL, si, u), ku = __shfl_sync(FULL, key, u);
+            if (lane == 0) { push_row(X, su, ku); push_col(X, su, ku); }
+        }
         __syncwarp();
     }
 
@@ -605,6 +707,14 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
     int Ls = lowest_slot(X, hi);
     int L = Ls >= 0 ? SLOTF(X, id, Ls) : -1;
     if (L != 0) err = RR_ERR_INTERNAL;
+    else {
+        if (lane == 0) { const int kk = SLOTF(X, key, Ls); unlink_row(X, Ls, kk); unlink_col(X, Ls, kk); }
+        __syncwarp();
+    }
+    // members: nm of them (leader excluded), on one line of type rowLine at
+    // index lineIdx, direction dm
+    int nm = 0, dm = -1, lineIdx = -1;
+    bool rowLine = true;
     const int64_t guard_max = I->n_steps + 2ll * k + 16;
     int64_t guard = 0;
 
@@ -613,75 +723,94 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
         int lr, lc, d, remL, lenL;
         move_pos(SLOTF(X, g0, Ls), SLOTF(X, g1, Ls), SLOTF(X, t, Ls), &lr, &lc, &d, &remL, &lenL);
         const int sgn = (d == 1 || d == 3) ? 1 : -1;
-        const int othersA = X.rowCnt[d * m + lr] - 1, othersB = X.colCnt[d * n + lc] - 1;
-        int kseg = remL, ns = 1;
-        long long *Mk = X.MkA;
-        if (othersA == 0 && othersB == 0) {
-            // the leader alone until the next waiting move of its direction
-            if (kseg > 1) {
-                const int hit = d >= 2 ? bit_scan(X.colBits + (d - 2) * X.Wn, n, lc, sgn, kseg - 1)
-                                       : bit_scan(X.rowBits + d * X.Wm, m, lr, sgn, kseg - 1);
-                if (hit > 0) kseg = hit;
-            }
-        } else {
-            int minA = INTMAX, minB = INTMAX, pickA = INTMAX, pickB = INTMAX, remA = INTMAX, remB = INTMAX;
-            int cntA = 0, cntB = 0;
-            auto visit = [&](int key, int id, int rem, int i) {
-                const bool same = (key & KEY_LIVE) && ((key >> 20) & 3) == d && i != Ls;
-                const int sr = key & 1023, sc = (key >> 10) & 1023;
-                const bool inA = same && sr == lr, inB = same && sc == lc;
-                if (inA) { minA = min(minA, id); remA = min(remA, rem); }
-                if (inB) { minB = min(minB, id); remB = min(remB, rem); }
-                const int dist = (d >= 2 ? sc - lc : sr - lr) * sgn;
-                if (same && dist > 0) {
-                    if (!inA) pickA = min(pickA, dist);
-                    if (!inB) pickB = min(pickB, dist);
-                }
-                const unsigned bA = __ballot_sync(FULL, inA), bB = __ballot_sync(FULL, inB);
-                const long long kv = ((long long)id << 32) | (unsigned)i;
-                if (inA && cntA + __popc(bA & lt) < lbuf) X.MkA[cntA + __popc(bA & lt)] = kv;
-                if (inB && cntB + __popc(bB & lt) < lbuf) X.MkB[cntB + __popc(bB & lt)] = kv;
-                cntA += __popc(bA);
-                cntB += __popc(bB);
-            };
-            const int hs = min(hi, X.C);
-            int i0 = 0;
-            for (; i0 + 128 <= hs; i0 += 128) {
-                int kk[4], id[4], le[4], tt[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = i0 + 32 * u + lane;
-                    kk[u] = X.sm.key[i]; id[u] = X.sm.id[i]; le[u] = X.sm.legEnd[i]; tt[u] = X.sm.t[i];
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) visit(kk[u], id[u], le[u] - tt[u], i0 + 32 * u + lane);
-            }
-            for (; i0 < hi; i0 += 32) {
-                const int i = i0 + lane;
-                const bool ok = i < hi;
-                const int key = ok ? SLOTF(X, key, i) : 0;
-                const int id = ok ? SLOTF(X, id, i) : INTMAX;
-                const int rem = ok ? SLOTF(X, legEnd, i) - SLOTF(X, t, i) : 0;
-                visit(key, id, rem, i);
-            }
-            minA = warp_min(minA); minB = warp_min(minB);
-            pickA = warp_min(pickA); pickB = warp_min(pickB);
-            remA = warp_min(remA); remB = warp_min(remB);
-            if (cntA > lineCap || cntB > lineCap) { err = RR_ERR_INTERNAL; break; }
-            const bool useA = minA < minB;
-            kseg = min(kseg, useA ? min(remA, pickA) : min(remB, pickB));
-            Mk = useA ? X.MkA : X.MkB;
-            const int cnt = useA ? cntA : cntB;
-            __syncwarp();
-            warp_sort64(Mk, cnt);
-            for (int u = lane; u < cnt; u += 32) X.M[1 + u] = (int)(Mk[u] & 0xffffffff);
-            ns = 1 + cnt;
+        // members still on the leader's line in the leader's direction?
+        if (nm > 0 && !(dm == d && (rowLine ? lineIdx == lr : lineIdx == lc))) { dissolve(X, nm, rowLine); nm = 0; }
+        // smallest static id on the leader's row and column (lane 0 walks)
+        int minA = INTMAX, minB = INTMAX;
+        const int hA = X.rowHead[d * m + lr], hB = X.colHead[d * n + lc];
+        if (lane == 0) {
+            int walk = 0;
+            for (int p = hA; p >= 0 && walk <= lineCap; p = SLOTF(X, rn, p), ++walk) minA = min(minA, SLOTF(X, id, p));
+            for (int p = hB; p >= 0 && walk <= 2 * lineCap; p = SLOTF(X, cn, p), ++walk) minB = min(minB, SLOTF(X, id, p));
+            if (walk > 2 * lineCap) err = RR_ERR_INTERNAL;
         }
-        if (lane == 0) X.M[0] = Ls;
-        __syncwarp();
+        minA = __shfl_sync(FULL, minA, 0);
+        minB = __shfl_sync(FULL, minB, 0);
+        err = __shfl_sync(FULL, err, 0);
+        if (err) break;
+        if (nm > 0) { if (rowLine) minA = min(minA, X.Mid[0]); else minB = min(minB, X.Mid[0]); }
+        if (minA != INTMAX || minB != INTMAX) {
+            const bool chooseRow = minA < minB;
+            if (nm > 0 && chooseRow != rowLine) { dissolve(X, nm, rowLine); nm = 0; }
+            // newcomers: every static of the chosen line (the list empties)
+            const int h = chooseRow ? X.rowHead[d * m + lr] : X.colHead[d * n + lc];
+            int nc = 0;
+            if (lane == 0) {
+                for (int p = h; p >= 0 && nc <= lineCap; p = chooseRow ? SLOTF(X, rn, p) : SLOTF(X, cn, p))
+                    X.Kb[nc++] = ((long long)SLOTF(X, id, p) << 32) | (unsigned)p;
+                if (chooseRow) {
+                    X.rowHead[d * m + lr] = -1;
+                    if (d < 2) atomicAnd(&X.rowBits[d * X.Wm + (lr >> 5)], ~(1u << (lr & 31)));
+                } else {
+                    X.colHead[d * n + lc] = -1;
+                    if (d >= 2) atomicAnd(&X.colBits[(d - 2) * X.Wn + (lc >> 5)], ~(1u << (lc & 31)));
+                }
+            }
+            nc = __shfl_sync(FULL, nc, 0);
+            if (nm + nc > lineCap) { err = RR_ERR_INTERNAL; break; }
+            __syncwarp();
+            // unlink each newcomer from its perpendicular list (distinct lists)
+            for (int u = lane; u < nc; u += 32) {
+                const int si = (int)(X.Kb[u] & 0xffffffff);
+                const int key = SLOTF(X, key, si);
+                if (chooseRow) unlink_col(X, si, key); else unlink_row(X, si, key);
+                SLOTF(X, key, si) = key | KEY_MEM;
+                prefetch_succ(ws, SLOTF(X, s4, si), SLOTF(X, nsucc, si));
+            }
+            __syncwarp();
+            warp_sort64(X.Kb, nc);
+            // merge the sorted newcomers into the sorted members
+            if (nc > 0) {
+                const int tot = nm + nc;
+                long long *out = X.Kb + (lineCap + 2);
+                for (int u = lane; u < nm; u += 32) {          // member u: rank among newcomers
+                    const long long key = ((long long)X.Mid[u] << 32) | (unsigned)X.Msl[u];
+                    int lo = 0, hi2 = nc;
+                    while (lo < hi2) { const int md = (lo + hi2) >> 1; if (X.Kb[md] < key) lo = md + 1; else hi2 = md; }
+                    out[u + lo] = key;
+                }
+                for (int u = lane; u < nc; u += 32) {          // newcomer u: rank among members
+                    const long long key = X.Kb[u];
+                    int lo = 0, hi2 = nm;
+                    while (lo < hi2) {
+                        const int md = (lo + hi2) >> 1;
+                        if ((((long long)X.Mid[md] << 32) | (unsigned)X.Msl[md]) < key) lo = md + 1; else hi2 = md;
+                    }
+                    out[u + lo] = key;
+                }
+                __syncwarp();
+                for (int u = lane; u < tot; u += 32) { X.Mid[u] = (int)(out[u] >> 32); X.Msl[u] = (int)(out[u] & 0xffffffff); }
+                nm = tot;
+            }
+            rowLine = chooseRow;
+            lineIdx = chooseRow ? lr : lc;
+            dm = d;
+            __syncwarp();
+        }
+        // segment length: shortest remaining leg, next pickup
+        int kseg = remL;
+        int remM = INTMAX;
+        for (int u = lane; u < nm; u += 32) { const int si = X.Msl[u]; remM = min(remM, SLOTF(X, legEnd, si) - SLOTF(X, t, si)); }
+        kseg = min(kseg, warp_min(remM));
+        if (kseg > 1) {   // a static move of direction d the leader's line reaches
+            const int hit = d >= 2 ? bit_scan(X.colBits + (d - 2) * X.Wn, n, lc, sgn, kseg - 1)
+                                   : bit_scan(X.rowBits + d * X.Wm, m, lr, sgn, kseg - 1);
+            if (hit > 0) kseg = hit;
+        }
         if (kseg < 1) { err = RR_ERR_INTERNAL; break; }
+        const int ns = nm + 1;
 
-        // kseg identical batches: the leader, then the line in ascending id
+        // kseg identical batches: the leader, then the members in ascending id
         const int64_t addm = (int64_t)kseg * ns;
         if (!overflow && nop + kseg <= cap_ops && nmem + addm <= cap_mem) {
             for (int i = lane; i < kseg; i += 32) ops[nop + i] = rr_op{d, (int32_t)(nmem + (int64_t)i * ns), ns};
@@ -691,7 +820,7 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
                 int u = lane % ns;
                 const int step = 32 % ns;
                 for (int64_t i = lane; i < addm; i += 32) {
-                    mem[nmem + i] = u == 0 ? L : (int)(Mk[u - 1] >> 32);
+                    mem[nmem + i] = u == 0 ? L : X.Mid[u - 1];
                     u += step;
                     if (u >= ns) u -= ns;
                 }
@@ -702,31 +831,44 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
         nop += kseg;
         nmem += addm;
 
-        // advance every member; finished ones release their successors
-        int leaderDone = 0;
+        // advance: u = 0 is the leader, u >= 1 member u-1. Finished moves
+        // release their successors; members whose leg ended leave the batch
+        // and become statics; the others stay members.
+        int leaderDone = 0, nkeep = 0;
         for (int u0 = 0; u0 < ns; u0 += 32) {
             const int u = u0 + lane;
-            bool fin = false, act = u < ns;
-            int si = -1, nsu = 0, newKey = 0, newLeg = 0, t = 0;
+            bool fin = false, turn = false, act = u < ns;
+            int si = -1, nsu = 0, newKey = 0;
             if (act) {
-                si = X.M[u];
-                t = SLOTF(X, t, si) + kseg;
+                si = u == 0 ? Ls : X.Msl[u - 1];
+                const int t = SLOTF(X, t, si) + kseg;
                 int r_, c_, d_, rem, len;
                 move_pos(SLOTF(X, g0, si), SLOTF(X, g1, si), t, &r_, &c_, &d_, &rem, &len);
+                SLOTF(X, t, si) = (int16_t)t;
                 fin = t >= len;
-                newKey = key_of(r_, c_, d_);
-                newLeg = t + rem;
-                cnt_add(X, SLOTF(X, key, si), -1);
-            }
-            __syncwarp();
-            if (act) {
-                SLOTF(X, t, si) = t;
                 if (fin) nsu = SLOTF(X, nsucc, si);
-                else { SLOTF(X, key, si) = newKey; SLOTF(X, legEnd, si) = newLeg; cnt_add(X, newKey, +1); }
+                else {
+                    turn = u > 0 && d_ != d;
+                    newKey = key_of(r_, c_, d_) | (u > 0 && !turn ? KEY_MEM : 0);
+                    SLOTF(X, key, si) = newKey;
+                    SLOTF(X, legEnd, si) = (int16_t)(t + rem);
+                }
             }
             if (u0 == 0 && __shfl_sync(FULL, (int)fin, 0)) leaderDone = 1;
+            // survivors keep their order (stable compaction into Kb)
+            const bool keep = act && u > 0 && !fin && !turn;
+            const unsigned kb = __ballot_sync(FULL, keep);
+            if (keep) X.Kb[nkeep + __popc(kb & lt)] = ((long long)X.Mid[u - 1] << 32) | (unsigned)si;
+            nkeep += __popc(kb);
+            // members whose leg ended become statics (lane 0, in order)
+            const unsigned tb = __ballot_sync(FULL, turn);
+            for (unsigned b = tb; b; b &= b - 1) {
+                const int w = __ffs(b) - 1;
+                const int sw = __shfl_sync(FULL, si, w), kw = __shfl_sync(FULL, newKey, w);
+                if (lane == 0) { push_row(X, sw, kw); push_col(X, sw, kw); }
+            }
             __syncwarp();
-            // successor entries of the finished members, in rounds of SBUF
+            // successor entries of the finished moves, in rounds of SBUF
             const int off = warp_incl_scan(nsu) - nsu;
             const int total = __shfl_sync(FULL, off + nsu, 31);
             for (int base = 0; base < total; base += SBUF) {
@@ -746,19 +888,26 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
                         int32_t e = X.sbuf[b0 + lane];
                         if (e < 0) e = ws.succ[~e];
                         const int id = e & SUCC_ID;
-                        r = ws.rec[id]; s4 = ws.succ4[id];     // fetched with the counter update
+                        r = ws.rec[2 * id]; s4 = ws.rec[2 * id + 1];   // fetched with the counter update
                         if ((e & SUCC_SINGLE) || atomicSub(&ws.indeg[id], 1) == 1) ready = id;
                     }
                     const unsigned bal = __ballot_sync(FULL, ready >= 0);
                     const int cnt = __popc(bal);
                     if (cnt) {
                         const int ns_ = alloc_slot(X, __popc(bal & lt), cnt, freeTop, ovfUsed, hi, k, &err);
-                        if (ready >= 0) fill_slot(X, ns_, ready, r, s4);
+                        int key = 0;
+                        if (ready >= 0) key = fill_slot(X, ns_, ready, r, s4);
+                        __syncwarp();
+                        for (unsigned b = bal; b; b &= b - 1) {
+                            const int w = __ffs(b) - 1;
+                            const int sw = __shfl_sync(FULL, ns_, w), kw = __shfl_sync(FULL, key, w);
+                            if (lane == 0) { push_row(X, sw, kw); push_col(X, sw, kw); }
+                        }
                     }
                     __syncwarp();
                 }
             }
-            // free the finished members' slots (shared-memory ones are recycled)
+            // free the finished moves' slots (shared-memory ones are recycled)
             if (fin) {
                 const int id = SLOTF(X, id, si);
                 if (X.map[id & (MAPN - 1)] == si) X.map[id & (MAPN - 1)] = -1;
@@ -767,12 +916,19 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
             }
             const bool recyc = fin && si < X.C;
             const unsigned fb = __ballot_sync(FULL, recyc);
-            if (recyc) X.freeStk[freeTop + __popc(fb & lt)] = si;
+            if (recyc) X.freeStk[freeTop + __popc(fb & lt)] = (int16_t)si;
             freeTop += __popc(fb);
             __syncwarp();
         }
+        for (int u = lane; u < nkeep; u += 32) { X.Mid[u] = (int)(X.Kb[u] >> 32); X.Msl[u] = (int)(X.Kb[u] & 0xffffffff); }
+        nm = nkeep;
+        // a line moving across itself carries its index along
+        if (rowLine && d < 2) lineIdx += sgn * kseg;
+        if (!rowLine && d >= 2) lineIdx += sgn * kseg;
+        __syncwarp();
         if (leaderDone && !err) {
-            // next leader: lowest id still held in a slot (usually L + 1)
+            // next leader: the lowest id still held (usually L + 1); a member
+            // leader leaves the front of the members, a static one its lists
             int cand = -1;
             const int nx = L + 1;
             if (nx < k) {
@@ -781,7 +937,24 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, int slotCap, int
             }
             if (cand < 0) cand = lowest_slot(X, hi);
             if (cand < 0) L = k;
-            else { Ls = cand; L = SLOTF(X, id, Ls); }
+            else {
+                Ls = cand;
+                L = SLOTF(X, id, Ls);
+                if (lane == 0) prefetch_succ(ws, SLOTF(X, s4, Ls), SLOTF(X, nsucc, Ls));
+                const int kk = SLOTF(X, key, Ls);
+                if (kk & KEY_MEM) {
+                    if (nm == 0 || X.Msl[0] != Ls) { err = RR_ERR_INTERNAL; break; }
+                    __syncwarp();
+                    for (int u = lane; u + 1 < nm; u += 32) X.Kb[u] = ((long long)X.Mid[u + 1] << 32) | (unsigned)X.Msl[u + 1];
+                    __syncwarp();
+                    --nm;
+                    for (int u = lane; u < nm; u += 32) { X.Mid[u] = (int)(X.Kb[u] >> 32); X.Msl[u] = (int)(X.Kb[u] & 0xffffffff); }
+                    if (lane == 0) SLOTF(X, key, Ls) = kk & ~KEY_MEM;
+                } else if (lane == 0) {
+                    unlink_row(X, Ls, kk);
+                    unlink_col(X, Ls, kk);
+                }
+            }
         }
         __syncwarp();
     }

@@ -22,7 +22,8 @@ __global__ void k_bsucc_count(rr_instance *, JobWS *, int);
 __global__ void k_bsucc_scan(rr_instance *, JobWS *, int, Arena);
 __global__ void k_bsucc_fill(rr_instance *, JobWS *, int);
 __global__ void k_brec(rr_instance *, JobWS *, int);
-__global__ void k_sim(rr_instance *, JobWS *, int, int, int);
+__global__ void k_classify(rr_instance *, int, int, const int *, int *, int *);
+__global__ void k_sim(rr_instance *, JobWS *, int, const int *, const int *, int, int);
 }  // namespace rrk
 
 using namespace rrk;
@@ -38,6 +39,13 @@ struct rr_ctx {
     JobWS *d_ws;
     int ws_cap;
     char err[256];
+    // simulation size classes: side bounds, counts and lists (device), and a
+    // stream per class forked from / joined into the caller's stream
+    static const int NCLASS = 4;
+    int *d_classSide, *d_classCount, *d_classList;
+    int classListCap;
+    cudaStream_t classStream[NCLASS];
+    cudaEvent_t evFork, evJoin[NCLASS];
     // stage tracing: events recorded on the launching stream around every kernel
     int tracing;
     int nmarks;
@@ -80,6 +88,9 @@ static int ensure_ws(rr_ctx *ctx, int count)
     ctx->d_ws = nullptr;
     ctx->ws_cap = 0;
     CUDA_TRY(cudaMalloc(&ctx->d_ws, sizeof(JobWS) * (size_t)cap));
+    if (ctx->d_classList) CUDA_TRY(cudaFree(ctx->d_classList));
+    ctx->d_classList = nullptr;
+    CUDA_TRY(cudaMalloc(&ctx->d_classList, sizeof(int) * (size_t)cap * rr_ctx::NCLASS));
     ctx->ws_cap = cap;
     return RR_OK;
 }
@@ -108,6 +119,13 @@ extern "C" int rr_ctx_create(rr_ctx **out, int64_t arena_bytes)
     ctx->arena_size = (unsigned long long)arena_bytes;
     int st = ensure_ws(ctx, 1);
     if (st != RR_OK) { rr_ctx_destroy(ctx); return st; }
+    bool ok = cudaMalloc(&ctx->d_classSide, sizeof(int) * rr_ctx::NCLASS) == cudaSuccess &&
+              cudaMalloc(&ctx->d_classCount, sizeof(int) * rr_ctx::NCLASS) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ctx->evFork, cudaEventDisableTiming) == cudaSuccess;
+    for (int c = 0; ok && c < rr_ctx::NCLASS; ++c)
+        ok = cudaStreamCreateWithFlags(&ctx->classStream[c], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ctx->evJoin[c], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) { rr_ctx_destroy(ctx); return fail(nullptr, RR_ERR_CUDA, "rr_ctx_create: stream/event setup failed"); }
     *out = ctx;
     return RR_OK;
 }
@@ -119,6 +137,14 @@ extern "C" int rr_ctx_destroy(rr_ctx *ctx)
     cudaFree(ctx->d_top);
     cudaFree(ctx->d_one);
     cudaFree(ctx->d_ws);
+    cudaFree(ctx->d_classSide);
+    cudaFree(ctx->d_classCount);
+    cudaFree(ctx->d_classList);
+    if (ctx->evFork) cudaEventDestroy(ctx->evFork);
+    for (int c = 0; c < rr_ctx::NCLASS; ++c) {
+        if (ctx->classStream[c]) cudaStreamDestroy(ctx->classStream[c]);
+        if (ctx->evJoin[c]) cudaEventDestroy(ctx->evJoin[c]);
+    }
     for (int i = 0; i < 32; ++i) if (ctx->marks[i]) cudaEventDestroy(ctx->marks[i]);
     delete ctx;
     return RR_OK;
@@ -186,19 +212,40 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
     k_bsucc_fill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
     mark(ctx, s, "k_brec");
     k_brec<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
-    // simulation: one warp per instance; ready-move slots, line lists and
-    // buffers in shared memory (layout mirrored in k_sim)
-    const int slotCap = 2 * max_side + 64, lineCap = max_side;
-    // per slot: s4 (16 B), eight int32 fields and a free-stack entry; two
-    // candidate-line buffers of 2 (lineCap + 2) int64; id map; member list;
-    // successor buffer; line counters [4][m] + [4][n]; pickup bitmaps
-    const size_t simSmem = 16ull * slotCap + 2ull * 8 * 2 * (lineCap + 2) + 4ull * 9 * slotCap + 4ull * 1024 +
-                           4ull * (lineCap + 2) + 4ull * 512 + 4ull * 8 * lineCap + 4ull * 4 * ((lineCap + 31) / 32) +
-                           64;
-    if (simSmem > 227 * 1024) return fail(ctx, RR_ERR_ARG, "simulation shared memory %zu too large", simSmem);
-    CUDA_TRY(cudaFuncSetAttribute(k_sim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)simSmem));
+    // simulation: one warp per instance, launched per size class on forked
+    // streams so that each class's shared memory fits its own grids; slot
+    // table, static lists and buffers live in shared memory (layout mirrored
+    // in k_sim)
+    int sides[rr_ctx::NCLASS];
+    for (int c = 0; c < rr_ctx::NCLASS; ++c) sides[c] = std::max(32, (max_side * (c + 1) + rr_ctx::NCLASS - 1) / rr_ctx::NCLASS);
+    sides[rr_ctx::NCLASS - 1] = max_side;
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_classSide, sides, sizeof(sides), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(ctx->d_classCount, 0, sizeof(int) * rr_ctx::NCLASS, s));
+    mark(ctx, s, "k_classify");
+    k_classify<<<(count + 255) / 256, 256, 0, s>>>(d_inst, count, rr_ctx::NCLASS, ctx->d_classSide, ctx->d_classCount,
+                                                  ctx->d_classList);
     mark(ctx, s, "k_sim");
-    k_sim<<<count, 32, simSmem, s>>>(d_inst, ctx->d_ws, count, slotCap, lineCap);
+    CUDA_TRY(cudaEventRecord(ctx->evFork, s));
+    for (int c = rr_ctx::NCLASS - 1; c >= 0; --c) {
+        cudaStream_t cs = ctx->classStream[c];
+        CUDA_TRY(cudaStreamWaitEvent(cs, ctx->evFork, 0));
+        const int side = sides[c];
+        // ready moves never exceed two per column here (one chain head each
+        // way); beyond the capacity slots spill to the global overflow area
+        const int slotCap = 2 * side + 8, lineCap = side;
+        // per slot: s4 (16 B), nine int32 and four int16 fields; sort / merge
+        // buffer 2 (lineCap + 2) int64; id map; member ids and slots; successor
+        // buffer; static list heads [4][m] + [4][n]; pickup bitmaps
+        const size_t simSmem = 16ull * slotCap + 8ull * 2 * (lineCap + 2) + 4ull * 9 * slotCap + 2ull * 4 * slotCap +
+                               4ull * 512 + 4ull * 2 * (lineCap + 2) + 4ull * 512 + 4ull * 8 * lineCap +
+                               4ull * 4 * ((lineCap + 31) / 32) + 64;
+        if (simSmem > 227 * 1024) return fail(ctx, RR_ERR_ARG, "simulation shared memory %zu too large", simSmem);
+        CUDA_TRY(cudaFuncSetAttribute(k_sim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)simSmem));
+        k_sim<<<count, 32, simSmem, cs>>>(d_inst, ctx->d_ws, count, ctx->d_classList + (size_t)c * count,
+                                         ctx->d_classCount + c, slotCap, lineCap);
+        CUDA_TRY(cudaEventRecord(ctx->evJoin[c], cs));
+        CUDA_TRY(cudaStreamWaitEvent(s, ctx->evJoin[c], 0));
+    }
     mark(ctx, s, nullptr);
     CUDA_TRY(cudaGetLastError());
     return RR_OK;
