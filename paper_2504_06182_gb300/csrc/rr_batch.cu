@@ -118,10 +118,16 @@ __global__ void k_bsetup(rr_instance *inst, JobWS *wsv, int count, Arena A)
             const unsigned long long cells = (unsigned long long)m * n;
             ws.P = tp;
             ws.pairOff = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
-            ws.cellCnt = (int32_t *)arena_alloc(A, 4ull * (cells + 1), &ok);
-            ws.cellCur = (int32_t *)arena_alloc(A, 4ull * cells, &ok);
-            ws.cover = (int32_t *)arena_alloc(A, 4ull * (tp + 1), &ok);
+            ws.cellCnt = nullptr; ws.cellCur = nullptr; ws.cover = nullptr;   // only if the sweeps do not apply
+            ws.genericGamma = 0;
             ws.nextAt = (int32_t *)arena_alloc(A, 4ull * (tp + 1), &ok);
+            ws.colOff = (int32_t *)arena_alloc(A, 4ull * (n + 1), &ok);
+            ws.colCur = (int32_t *)arena_alloc(A, 4ull * (n + 1), &ok);
+            ws.colList = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
+            ws.rowOff = (int32_t *)arena_alloc(A, 4ull * (m + 1), &ok);
+            ws.rowCur = (int32_t *)arena_alloc(A, 4ull * (m + 1), &ok);
+            ws.rowList = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
+            ws.firstH = (int32_t *)arena_alloc(A, 4ull * cells, &ok);
             ws.succOff = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
             ws.indeg = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
             ws.rec = (int4 *)arena_alloc(A, 32ull * (k + 1), &ok);   // record, successors: one 32 B sector
@@ -141,11 +147,248 @@ __global__ void k_bsetup(rr_instance *inst, JobWS *wsv, int count, Arena A)
         ws.indeg[b] = 0;
     }
     if (threadIdx.x == 0) ws.ready0[k] = 0;      // count of initially ready moves
-    const long long cells = (long long)m * n;
-    for (long long v = threadIdx.x; v < cells; v += blockDim.x) { ws.cellCnt[v] = 0; ws.cellCur[v] = 0; }
+    for (int c = threadIdx.x; c <= n; c += blockDim.x) { ws.colOff[c] = 0; ws.colCur[c] = 0; }
+    for (int r = threadIdx.x; r <= m; r += blockDim.x) { ws.rowOff[r] = 0; ws.rowCur[r] = 0; }
     __syncthreads();
     const long long tot = block_exclusive_scan(ws.pairOff, (int)k, s_tmp);
     if (threadIdx.x == 0) ws.pairOff[k] = (int32_t)tot;
+}
+
+// ---------------------------------------------------------------- Gamma
+// Vertex (r, c) is covered by the vertical parts of the moves ending in
+// column c (the corner of an L-move included) and by the horizontal parts of
+// the L-moves running along row r (their destination column excluded). When
+// every move of the first kind precedes every move of the second kind at
+// each vertex -- always so for red-rec plans, since a corridor only crosses
+// a column after that column's moves were emitted -- the next path through a
+// vertex follows from two sweeps in id order: one per column over the moves
+// ending there, one per row over the L-moves on it. The column sweep checks
+// that order at every vertex; an instance that breaks it falls back to
+// per-vertex path lists.
+
+__global__ void k_gcount(rr_instance *inst, JobWS *wsv, int count)
+{
+    const int q = blockIdx.y;
+    if (q >= count) return;
+    const rr_instance *I = &inst[q];
+    if (!live(I)) return;
+    JobWS &ws = wsv[q];
+    const int64_t k = I->n_moves;
+    for (int64_t b = blockIdx.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)gridDim.x * blockDim.x) {
+        const rr_move p = I->moves[b];
+        atomicAdd(&ws.colCur[p.dst_col], 1);
+        if (p.src_col != p.dst_col) atomicAdd(&ws.rowCur[p.src_row], 1);
+    }
+}
+
+__global__ void k_gscan(rr_instance *inst, JobWS *wsv, int count)
+{
+    const int q = blockIdx.x;
+    if (q >= count) return;
+    const rr_instance *I = &inst[q];
+    if (!live(I)) return;
+    JobWS &ws = wsv[q];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid > 1) return;
+    // warp 0: columns, warp 1: rows
+    const int len = wid == 0 ? I->n : I->m;
+    int32_t *cnt = wid == 0 ? ws.colCur : ws.rowCur, *off = wid == 0 ? ws.colOff : ws.rowOff;
+    int carry = 0;
+    for (int base = 0; base < len; base += 32) {
+        const int i = base + lane;
+        const int v = i < len ? cnt[i] : 0;
+        const int incl = warp_incl_scan(v);
+        if (i < len) { off[i] = carry + incl - v; cnt[i] = carry + incl - v; }
+        carry += __shfl_sync(FULL, incl, 31);
+    }
+    if (lane == 0) off[len] = carry;
+}
+
+__global__ void k_gfill(rr_instance *inst, JobWS *wsv, int count)
+{
+    const int q = blockIdx.y;
+    if (q >= count) return;
+    const rr_instance *I = &inst[q];
+    if (!live(I)) return;
+    JobWS &ws = wsv[q];
+    const int64_t k = I->n_moves;
+    for (int64_t b = blockIdx.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)gridDim.x * blockDim.x) {
+        const rr_move p = I->moves[b];
+        ws.colList[atomicAdd(&ws.colCur[p.dst_col], 1)] = (int32_t)b;
+        if (p.src_col != p.dst_col) ws.rowList[atomicAdd(&ws.rowCur[p.src_row], 1)] = (int32_t)b;
+    }
+}
+
+// Sort a[0..n) of int32 ascending with one warp (registers up to 32, else a
+// shared-memory bitonic network over buf, sized for the next power of two).
+__device__ void warp_sort32(int32_t *a, int n, int32_t *buf)
+{
+    const int lane = threadIdx.x & 31;
+    if (n <= 1) return;
+    if (n <= 32) {
+        int v = lane < n ? a[lane] : 0x7fffffff;
+#pragma unroll
+        for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                const int o = __shfl_xor_sync(FULL, v, jj);
+                const bool up = (lane & kk) == 0, low = (lane & jj) == 0;
+                v = (low == up) ? min(v, o) : max(v, o);
+            }
+        }
+        if (lane < n) a[lane] = v;
+        __syncwarp();
+        return;
+    }
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = lane; i < P; i += 32) buf[i] = i < n ? a[i] : 0x7fffffff;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < P; i += 32) {
+                const int ij = i ^ j;
+                if (ij > i) {
+                    const int x = buf[i], y = buf[ij];
+                    if ((x > y) == ((i & k) == 0)) { buf[i] = y; buf[ij] = x; }
+                }
+            }
+            __syncwarp();
+        }
+    for (int i = lane; i < n; i += 32) a[i] = buf[i];
+    __syncwarp();
+}
+
+// Order every column list and row list by id (one warp per list). Lists of
+// red-rec plans are mostly ascending already.
+__global__ void k_gsort(rr_instance *inst, JobWS *wsv, int count, int bufLen)
+{
+    extern __shared__ int32_t sortbuf[];
+    const int q = blockIdx.y;
+    if (q >= count) return;
+    const rr_instance *I = &inst[q];
+    if (!live(I)) return;
+    JobWS &ws = wsv[q];
+    const int lane = threadIdx.x & 31;
+    int32_t *buf = sortbuf + (threadIdx.x >> 5) * bufLen;
+    const int nl = I->n + I->m;
+    for (int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); l < nl; l += gridDim.x * (blockDim.x >> 5)) {
+        const bool col = l < I->n;
+        const int idx = col ? l : l - I->n;
+        int32_t *a = col ? ws.colList + ws.colOff[idx] : ws.rowList + ws.rowOff[idx];
+        const int len = col ? ws.colOff[idx + 1] - ws.colOff[idx] : ws.rowOff[idx + 1] - ws.rowOff[idx];
+        bool sorted = true;
+        for (int i = lane; i + 1 < len; i += 32) sorted &= a[i] < a[i + 1];
+        if (__all_sync(FULL, sorted)) continue;
+        warp_sort32(a, len, buf);
+    }
+}
+
+// Row sweep: the L-moves along each row in id order; each vertex's
+// consecutive horizontal coverers are linked, the first is recorded.
+__global__ void k_gsweep_h(rr_instance *inst, JobWS *wsv, int count, int lineCap)
+{
+    extern __shared__ int32_t sweepbuf[];
+    const int q = blockIdx.y;
+    if (q >= count) return;
+    const rr_instance *I = &inst[q];
+    if (!live(I)) return;
+    JobWS &ws = wsv[q];
+    const int lane = threadIdx.x & 31;
+    const int n = I->n, m = I->m;
+    int32_t *lastPos = sweepbuf + (threadIdx.x >> 5) * lineCap;
+    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < m; r += gridDim.x * (blockDim.x >> 5)) {
+        for (int c = lane; c < n; c += 32) { lastPos[c] = -1; ws.firstH[(size_t)r * n + c] = -1; }
+        __syncwarp();
+        for (int e = ws.rowOff[r]; e < ws.rowOff[r + 1]; ++e) {
+            const int b = ws.rowList[e];
+            const rr_move p = I->moves[b];
+            const int step = p.dst_col > p.src_col ? 1 : -1;
+            const int hl = iabs(p.dst_col - p.src_col);
+            const int base = ws.pairOff[b];
+            for (int t = lane; t < hl; t += 32) {       // the destination column is the corner
+                const int c = p.src_col + t * step;
+                const int prev = lastPos[c];
+                if (prev >= 0) ws.nextAt[prev] = b;
+                else ws.firstH[(size_t)r * n + c] = b;
+                lastPos[c] = base + t;
+            }
+            __syncwarp();
+        }
+        for (int c = lane; c < n; c += 32)
+            if (lastPos[c] >= 0) ws.nextAt[lastPos[c]] = -1;
+        __syncwarp();
+    }
+}
+
+// Column sweep: the moves ending in each column in id order; consecutive
+// vertical coverers are linked, the last one to the vertex's first
+// horizontal coverer. Flags the instance if a horizontal coverer precedes a
+// vertical one anywhere.
+__global__ void k_gsweep_v(rr_instance *inst, JobWS *wsv, int count, int lineCap)
+{
+    extern __shared__ int32_t sweepbuf[];
+    const int q = blockIdx.y;
+    if (q >= count) return;
+    const rr_instance *I = &inst[q];
+    if (!live(I)) return;
+    JobWS &ws = wsv[q];
+    const int lane = threadIdx.x & 31;
+    const int n = I->n, m = I->m;
+    int32_t *lastPos = sweepbuf + (threadIdx.x >> 5) * 2 * lineCap;
+    int32_t *lastId = lastPos + lineCap;
+    for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n; c += gridDim.x * (blockDim.x >> 5)) {
+        for (int r = lane; r < m; r += 32) lastPos[r] = -1;
+        __syncwarp();
+        for (int e = ws.colOff[c]; e < ws.colOff[c + 1]; ++e) {
+            const int b = ws.colList[e];
+            const rr_move p = I->moves[b];
+            const int step = p.dst_row > p.src_row ? 1 : -1;
+            const int hl = iabs(p.dst_col - p.src_col), vl = iabs(p.dst_row - p.src_row);
+            const int base = ws.pairOff[b] + hl;
+            for (int t = lane; t <= vl; t += 32) {      // t = 0 is the corner / the source
+                const int r = p.src_row + t * step;
+                const int prev = lastPos[r];
+                if (prev >= 0) ws.nextAt[prev] = b;
+                lastPos[r] = base + t;
+                lastId[r] = b;
+            }
+            __syncwarp();
+        }
+        bool bad = false;
+        for (int r = lane; r < m; r += 32) {
+            if (lastPos[r] < 0) continue;
+            const int f = ws.firstH[(size_t)r * n + c];
+            bad |= f >= 0 && f < lastId[r];
+            ws.nextAt[lastPos[r]] = f;
+        }
+        if (__any_sync(FULL, bad) && lane == 0) ws.genericGamma = 1;
+        __syncwarp();
+    }
+}
+
+// Per-vertex lists for the instances the sweeps cannot serve.
+__global__ void k_galloc(rr_instance *inst, JobWS *wsv, int count, Arena A)
+{
+    const int q = blockIdx.x;
+    if (q >= count) return;
+    rr_instance *I = &inst[q];
+    if (!live(I)) return;
+    JobWS &ws = wsv[q];
+    if (!ws.genericGamma) return;
+    __shared__ int s_ok;
+    const unsigned long long cells = (unsigned long long)I->m * I->n;
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        ws.cellCnt = (int32_t *)arena_alloc(A, 4ull * (cells + 1), &ok);
+        ws.cellCur = (int32_t *)arena_alloc(A, 4ull * cells, &ok);
+        ws.cover = (int32_t *)arena_alloc(A, 4ull * (ws.P + 1), &ok);
+        s_ok = ok;
+        if (!ok) I->status = RR_ERR_WORKSPACE;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    for (unsigned long long v = threadIdx.x; v < cells; v += blockDim.x) { ws.cellCnt[v] = 0; ws.cellCur[v] = 0; }
 }
 
 // Vertex counts per cell.
@@ -156,6 +399,7 @@ __global__ void k_bcount(rr_instance *inst, JobWS *wsv, int count)
     const rr_instance *I = &inst[q];
     if (!live(I)) return;
     JobWS &ws = wsv[q];
+    if (!ws.genericGamma) return;
     const int n = I->n;
     const int64_t k = I->n_moves;
     for (int64_t b = blockIdx.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)gridDim.x * blockDim.x) {
@@ -176,6 +420,7 @@ __global__ void k_bscan_cells(rr_instance *inst, JobWS *wsv, int count)
     rr_instance *I = &inst[q];
     if (!live(I)) return;
     JobWS &ws = wsv[q];
+    if (!ws.genericGamma) return;
     const int cells = I->m * I->n;
     const long long tot = block_exclusive_scan(ws.cellCnt, cells, s_tmp);
     if (threadIdx.x == 0) {
@@ -191,6 +436,7 @@ __global__ void k_bfill(rr_instance *inst, JobWS *wsv, int count)
     const rr_instance *I = &inst[q];
     if (!live(I)) return;
     JobWS &ws = wsv[q];
+    if (!ws.genericGamma) return;
     const int n = I->n;
     const int64_t k = I->n_moves;
     for (int64_t b = blockIdx.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)gridDim.x * blockDim.x) {
@@ -213,6 +459,7 @@ __global__ void k_bsort(rr_instance *inst, JobWS *wsv, int count)
     const rr_instance *I = &inst[q];
     if (!live(I)) return;
     JobWS &ws = wsv[q];
+    if (!ws.genericGamma) return;
     const int n = I->n;
     const long long cells = (long long)I->m * n;
     for (long long v = blockIdx.x * blockDim.x + threadIdx.x; v < cells; v += (long long)gridDim.x * blockDim.x) {

@@ -14,6 +14,13 @@ __global__ void k_pair(rr_instance *, JobWS *, int);
 __global__ void k_emit_cols(rr_instance *, JobWS *, int);
 __global__ void k_emit_recv(rr_instance *, JobWS *, int);
 __global__ void k_bsetup(rr_instance *, JobWS *, int, Arena);
+__global__ void k_gcount(rr_instance *, JobWS *, int);
+__global__ void k_gscan(rr_instance *, JobWS *, int);
+__global__ void k_gfill(rr_instance *, JobWS *, int);
+__global__ void k_gsort(rr_instance *, JobWS *, int, int);
+__global__ void k_gsweep_h(rr_instance *, JobWS *, int, int);
+__global__ void k_gsweep_v(rr_instance *, JobWS *, int, int);
+__global__ void k_galloc(rr_instance *, JobWS *, int, Arena);
 __global__ void k_bcount(rr_instance *, JobWS *, int);
 __global__ void k_bscan_cells(rr_instance *, JobWS *, int);
 __global__ void k_bfill(rr_instance *, JobWS *, int);
@@ -196,6 +203,29 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
     const int cellBlocks = clampi(std::max(1, 8192 / count), 1, (max_side * max_side + 255) / 256);
     mark(ctx, s, "k_bsetup");
     k_bsetup<<<count, 512, 0, s>>>(d_inst, ctx->d_ws, count, A);
+    {
+        // Gamma by column and row sweeps (per-vertex lists only where they fail)
+        const int lineBlocks = clampi(std::max(1, 8192 / count), 1, (2 * max_side + 7) / 8);
+        mark(ctx, s, "k_gcount");
+        k_gcount<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+        mark(ctx, s, "k_gscan");
+        k_gscan<<<count, 64, 0, s>>>(d_inst, ctx->d_ws, count);
+        mark(ctx, s, "k_gfill");
+        k_gfill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+        int P2 = 32;
+        while (P2 < max_side) P2 <<= 1;
+        CUDA_TRY(cudaFuncSetAttribute(k_gsort, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 4 * P2));
+        CUDA_TRY(cudaFuncSetAttribute(k_gsweep_h, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 4 * max_side));
+        CUDA_TRY(cudaFuncSetAttribute(k_gsweep_v, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 8 * max_side));
+        mark(ctx, s, "k_gsort");
+        k_gsort<<<dim3(lineBlocks, count), 256, 8 * 4 * (size_t)P2, s>>>(d_inst, ctx->d_ws, count, P2);
+        mark(ctx, s, "k_gsweep_h");
+        k_gsweep_h<<<dim3(lineBlocks, count), 256, 8 * 4 * (size_t)max_side, s>>>(d_inst, ctx->d_ws, count, max_side);
+        mark(ctx, s, "k_gsweep_v");
+        k_gsweep_v<<<dim3(lineBlocks, count), 256, 8 * 8 * (size_t)max_side, s>>>(d_inst, ctx->d_ws, count, max_side);
+        mark(ctx, s, "k_galloc");
+        k_galloc<<<count, 256, 0, s>>>(d_inst, ctx->d_ws, count, A);
+    }
     mark(ctx, s, "k_bcount");
     k_bcount<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
     mark(ctx, s, "k_bscan_cells");

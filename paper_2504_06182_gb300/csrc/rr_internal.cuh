@@ -79,6 +79,11 @@ struct JobWS {
     int4 *rec;             // k: packed geometry, successor count, overflow offset
     int4 *succ4;           // k: first four successors (flagged, -1 padded)
     int32_t *ready0;       // k + 1: moves without predecessors; [k] = their count
+    // Gamma by sweeps: moves ending in each column, L-moves starting on each row
+    int32_t *colOff, *colCur, *colList;   // n + 1, n, k
+    int32_t *rowOff, *rowCur, *rowList;   // m + 1, m, k
+    int32_t *firstH;       // m * n: lowest-id L-move crossing each vertex, -1
+    int32_t genericGamma;  // set when the sweep order does not hold: per-vertex lists instead
     void *slotOvf;         // k simulation slots beyond the shared-memory ones
 };
 
