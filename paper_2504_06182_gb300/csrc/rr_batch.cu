@@ -134,6 +134,7 @@ __global__ void k_bsetup(rr_instance *inst, JobWS *wsv, int count, Arena A)
             ws.succ4 = ws.rec + 1;
             ws.ready0 = (int32_t *)arena_alloc(A, 4ull * (k + 1) + 16, &ok);
             ws.slotOvf = arena_alloc(A, 64ull * (k + 1), &ok);
+            ws.ovfFree = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
             ws.succ = nullptr; ws.E = 0;
             if (!ok) I->status = RR_ERR_WORKSPACE;
         }
@@ -609,7 +610,7 @@ constexpr int KEY_LIVE = 1 << 22;
 constexpr int KEY_MEM = 1 << 23;
 constexpr int INTMAX = 0x7fffffff;
 
-struct SlotSoA {
+template <typename IX> struct SlotSoA {
     int32_t *key;     // row | col << 10 | dir << 20 | KEY_LIVE [| KEY_MEM]; 0 when free
     int32_t *id;      // move id, INT_MAX when free
     int32_t *g0, *g1; // src_row | src_col << 16, dst_row | dst_col << 16
@@ -617,16 +618,17 @@ struct SlotSoA {
     int16_t *legEnd;  // t at the end of the current straight leg
     int16_t *nsucc;
     int32_t *ovf;
-    int32_t *rp, *rn, *cp, *cn;   // static-list links (slot indices, -1)
+    IX *rp, *rn, *cp, *cn;        // static-list links (slot indices, -1)
     int4 *s4;         // first four successors
 };
 
-struct Sim {
-    SlotSoA sm, gm;
+template <typename IX> struct Sim {
+    SlotSoA<IX> sm, gm;
     int C, m, n, Wm, Wn;
     int16_t *freeStk;
     int32_t *map;
-    int32_t *rowHead, *colHead;     // [4][m], [4][n] static lists
+    IX *rowHead, *colHead;          // [4][m], [4][n] static lists
+    int32_t *ovfFree;               // recycled overflow slots (global)
     uint32_t *rowBits, *colBits;    // [2][Wm] (dirs 0, 1), [2][Wn] (dirs 2, 3)
     int32_t *Mid, *Msl;             // members sorted by id
     long long *Kb;                  // sort / merge buffer
@@ -657,7 +659,8 @@ __device__ __forceinline__ int warp_min(int v)
     return v;
 }
 
-__device__ __forceinline__ void bits_set(const Sim &X, int d, int r, int c)
+template <typename IX>
+__device__ __forceinline__ void bits_set(const Sim<IX> &X, int d, int r, int c)
 {
     if (d < 2) atomicOr(&X.rowBits[d * X.Wm + (r >> 5)], 1u << (r & 31));
     else atomicOr(&X.colBits[(d - 2) * X.Wn + (c >> 5)], 1u << (c & 31));
@@ -666,36 +669,40 @@ __device__ __forceinline__ void bits_set(const Sim &X, int d, int r, int c)
 // Static-list maintenance. push/remove touch the row list and the column
 // list of the slot's current key; callers that run them on several lanes at
 // once must guarantee distinct lists (see dissolve()).
-__device__ void push_row(const Sim &X, int si, int key)
+template <typename IX>
+__device__ void push_row(const Sim<IX> &X, int si, int key)
 {
-    int32_t *h = &X.rowHead[key_d(key) * X.m + key_r(key)];
-    SLOTF(X, rp, si) = -1; SLOTF(X, rn, si) = *h;
-    if (*h >= 0) SLOTF(X, rp, *h) = si;
-    *h = si;
+    IX *h = &X.rowHead[key_d(key) * X.m + key_r(key)];
+    SLOTF(X, rp, si) = (IX)-1; SLOTF(X, rn, si) = *h;
+    if (*h >= 0) SLOTF(X, rp, *h) = (IX)si;
+    *h = (IX)si;
     if (key_d(key) < 2) atomicOr(&X.rowBits[key_d(key) * X.Wm + (key_r(key) >> 5)], 1u << (key_r(key) & 31));
 }
-__device__ void push_col(const Sim &X, int si, int key)
+template <typename IX>
+__device__ void push_col(const Sim<IX> &X, int si, int key)
 {
-    int32_t *h = &X.colHead[key_d(key) * X.n + key_c(key)];
-    SLOTF(X, cp, si) = -1; SLOTF(X, cn, si) = *h;
-    if (*h >= 0) SLOTF(X, cp, *h) = si;
-    *h = si;
+    IX *h = &X.colHead[key_d(key) * X.n + key_c(key)];
+    SLOTF(X, cp, si) = (IX)-1; SLOTF(X, cn, si) = *h;
+    if (*h >= 0) SLOTF(X, cp, *h) = (IX)si;
+    *h = (IX)si;
     if (key_d(key) >= 2) atomicOr(&X.colBits[(key_d(key) - 2) * X.Wn + (key_c(key) >> 5)], 1u << (key_c(key) & 31));
 }
-__device__ void unlink_row(const Sim &X, int si, int key)
+template <typename IX>
+__device__ void unlink_row(const Sim<IX> &X, int si, int key)
 {
     const int p = SLOTF(X, rp, si), q = SLOTF(X, rn, si);
-    int32_t *h = &X.rowHead[key_d(key) * X.m + key_r(key)];
-    if (p >= 0) SLOTF(X, rn, p) = q; else *h = q;
-    if (q >= 0) SLOTF(X, rp, q) = p;
+    IX *h = &X.rowHead[key_d(key) * X.m + key_r(key)];
+    if (p >= 0) SLOTF(X, rn, p) = (IX)q; else *h = (IX)q;
+    if (q >= 0) SLOTF(X, rp, q) = (IX)p;
     if (*h < 0 && key_d(key) < 2) atomicAnd(&X.rowBits[key_d(key) * X.Wm + (key_r(key) >> 5)], ~(1u << (key_r(key) & 31)));
 }
-__device__ void unlink_col(const Sim &X, int si, int key)
+template <typename IX>
+__device__ void unlink_col(const Sim<IX> &X, int si, int key)
 {
     const int p = SLOTF(X, cp, si), q = SLOTF(X, cn, si);
-    int32_t *h = &X.colHead[key_d(key) * X.n + key_c(key)];
-    if (p >= 0) SLOTF(X, cn, p) = q; else *h = q;
-    if (q >= 0) SLOTF(X, cp, q) = p;
+    IX *h = &X.colHead[key_d(key) * X.n + key_c(key)];
+    if (p >= 0) SLOTF(X, cn, p) = (IX)q; else *h = (IX)q;
+    if (q >= 0) SLOTF(X, cp, q) = (IX)p;
     if (*h < 0 && key_d(key) >= 2) atomicAnd(&X.colBits[(key_d(key) - 2) * X.Wn + (key_c(key) >> 5)], ~(1u << (key_c(key) & 31)));
 }
 
@@ -713,7 +720,8 @@ __device__ int bit_scan(const uint32_t *b, int limit, int pos, int delta, int ma
 }
 
 // Lowest move id held in slots [0, hi) and its slot (warp-cooperative).
-__device__ int lowest_slot(const Sim &X, int hi)
+template <typename IX>
+__device__ int lowest_slot(const Sim<IX> &X, int hi)
 {
     const int lane = threadIdx.x & 31;
     int best = INTMAX, bs = -1;
@@ -771,16 +779,25 @@ __device__ void warp_sort64(long long *a, int n)
 
 // Allocate `cnt` slots (warp-cooperative); lane `rank` < cnt gets a slot.
 // freeTop / ovfUsed / hi are warp-uniform.
-__device__ __forceinline__ int alloc_slot(const Sim &X, int rank, int cnt, int &freeTop, int &ovfUsed, int &hi,
-                                          int kmax, int *err)
+template <typename IX>
+__device__ __forceinline__ int alloc_slot(const Sim<IX> &X, int rank, int cnt, int &freeTop, int &ovfFreeTop,
+                                          int &ovfUsed, int &hi, int kmax, int *err)
 {
     int si = -1;
     const int fromStack = min(cnt, freeTop);
+    const int fromOvf = min(cnt - fromStack, ovfFreeTop);
     if (rank < fromStack) si = X.freeStk[freeTop - 1 - rank];
-    else if (rank < cnt) si = X.C + ovfUsed + (rank - fromStack);
+    else if (rank < fromStack + fromOvf) si = X.ovfFree[ovfFreeTop - 1 - (rank - fromStack)];
+    else if (rank < cnt) si = X.C + ovfUsed + (rank - fromStack - fromOvf);
     freeTop -= fromStack;
-    ovfUsed += cnt - fromStack;
-    if (ovfUsed > kmax) *err = RR_ERR_INTERNAL;
+    ovfFreeTop -= fromOvf;
+    ovfUsed += cnt - fromStack - fromOvf;
+    // the overflow area holds kmax + 1 slots, and slot indices must stay
+    // representable in the link type: beyond either, no slot (nothing is
+    // written) and the run ends with an error
+    const int lastOk = min(X.C + kmax, sizeof(IX) == 2 ? 32767 : 0x7fffffff);
+    if (si > lastOk) si = -1;
+    if (ovfUsed > kmax || X.C + ovfUsed > lastOk + 1) *err = RR_ERR_INTERNAL;
     int top = si + 1;
 #pragma unroll
     for (int o = 16; o; o >>= 1) top = max(top, __shfl_xor_sync(FULL, top, o));
@@ -789,7 +806,8 @@ __device__ __forceinline__ int alloc_slot(const Sim &X, int rank, int cnt, int &
 }
 
 // A newly ready move: fill its slot (the caller links it into the lists).
-__device__ __forceinline__ int fill_slot(const Sim &X, int si, int id, int4 r, int4 s4)
+template <typename IX>
+__device__ __forceinline__ int fill_slot(const Sim<IX> &X, int si, int id, int4 r, int4 s4)
 {
     int rr, cc, d, rem, len;
     move_pos(r.x, r.y, 0, &rr, &cc, &d, &rem, &len);
@@ -823,12 +841,13 @@ __device__ __forceinline__ void prefetch_succ(const JobWS &ws, int4 s4, int nsuc
 // Turn the members back into statics (warp-cooperative). Members share one
 // line, so their perpendicular lists are distinct and are pushed in
 // parallel; the shared line list gets the members as one spliced chain.
-__device__ void dissolve(const Sim &X, int nm, bool rowLine)
+template <typename IX>
+__device__ void dissolve(const Sim<IX> &X, int nm, bool rowLine)
 {
     const int lane = threadIdx.x & 31;
     if (nm <= 0) return;
     const int k0 = SLOTF(X, key, X.Msl[0]) & ~KEY_MEM;
-    int32_t *lineHead = rowLine ? &X.rowHead[key_d(k0) * X.m + key_r(k0)] : &X.colHead[key_d(k0) * X.n + key_c(k0)];
+    IX *lineHead = rowLine ? &X.rowHead[key_d(k0) * X.m + key_r(k0)] : &X.colHead[key_d(k0) * X.n + key_c(k0)];
     const int oldHead = *lineHead;
     __syncwarp();
     for (int u = lane; u < nm; u += 32) {
@@ -836,13 +855,13 @@ __device__ void dissolve(const Sim &X, int nm, bool rowLine)
         const int key = SLOTF(X, key, si) & ~KEY_MEM;
         SLOTF(X, key, si) = key;
         const int prv = u == 0 ? -1 : X.Msl[u - 1], nxt = u == nm - 1 ? oldHead : X.Msl[u + 1];
-        if (rowLine) { SLOTF(X, rp, si) = prv; SLOTF(X, rn, si) = nxt; push_col(X, si, key); }
-        else { SLOTF(X, cp, si) = prv; SLOTF(X, cn, si) = nxt; push_row(X, si, key); }
+        if (rowLine) { SLOTF(X, rp, si) = (IX)prv; SLOTF(X, rn, si) = (IX)nxt; push_col(X, si, key); }
+        else { SLOTF(X, cp, si) = (IX)prv; SLOTF(X, cn, si) = (IX)nxt; push_row(X, si, key); }
     }
     __syncwarp();
     if (lane == 0) {
-        if (oldHead >= 0) { if (rowLine) SLOTF(X, rp, oldHead) = X.Msl[nm - 1]; else SLOTF(X, cp, oldHead) = X.Msl[nm - 1]; }
-        *lineHead = X.Msl[0];
+        if (oldHead >= 0) { if (rowLine) SLOTF(X, rp, oldHead) = (IX)X.Msl[nm - 1]; else SLOTF(X, cp, oldHead) = (IX)X.Msl[nm - 1]; }
+        *lineHead = (IX)X.Msl[0];
         bits_set(X, key_d(k0), key_r(k0), key_c(k0));
     }
     __syncwarp();
@@ -863,8 +882,9 @@ __global__ void k_classify(rr_instance *inst, int count, int nclass, const int *
     }
 }
 
-__global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, const int *classList, const int *classCount,
-                      int slotCap, int lineCap)
+template <typename IX>
+__device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int count, const int *classList,
+                                         const int *classCount, int slotCap, int lineCap)
 {
     extern __shared__ int4 smem_i4[];
     if ((int)blockIdx.x >= *classCount) return;
@@ -880,7 +900,7 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, const int *class
     if (k == 0) { if (lane == 0) { I->n_ops = 0; I->n_members = 0; } return; }
 
     // shared-memory layout (mirrored by the launcher's size computation)
-    Sim X;
+    Sim<IX> X;
     X.C = slotCap; X.m = m; X.n = n; X.Wm = (m + 31) >> 5; X.Wn = (n + 31) >> 5;
     const int lbuf = 2 * (lineCap + 2);
     X.sm.s4 = smem_i4;
@@ -891,40 +911,44 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, const int *class
     X.sm.g0 = p32; p32 += slotCap;
     X.sm.g1 = p32; p32 += slotCap;
     X.sm.ovf = p32; p32 += slotCap;
-    X.sm.rp = p32; p32 += slotCap;
-    X.sm.rn = p32; p32 += slotCap;
-    X.sm.cp = p32; p32 += slotCap;
-    X.sm.cn = p32; p32 += slotCap;
     X.map = p32; p32 += MAPN;
     X.Mid = p32; p32 += lineCap + 2;
     X.Msl = p32; p32 += lineCap + 2;
     X.sbuf = p32; p32 += SBUF;
-    X.rowHead = p32; p32 += 4 * lineCap;
-    X.colHead = p32; p32 += 4 * lineCap;
     X.rowBits = (uint32_t *)p32; p32 += 2 * ((lineCap + 31) >> 5);
     X.colBits = (uint32_t *)p32; p32 += 2 * ((lineCap + 31) >> 5);
-    int16_t *p16 = (int16_t *)p32;
+    IX *pix = (IX *)p32;
+    X.sm.rp = pix; pix += slotCap;
+    X.sm.rn = pix; pix += slotCap;
+    X.sm.cp = pix; pix += slotCap;
+    X.sm.cn = pix; pix += slotCap;
+    X.rowHead = pix; pix += 4 * lineCap;
+    X.colHead = pix; pix += 4 * lineCap;
+    int16_t *p16 = (int16_t *)pix;
     X.sm.t = p16; p16 += slotCap;
     X.sm.legEnd = p16; p16 += slotCap;
     X.sm.nsucc = p16; p16 += slotCap;
     X.freeStk = p16;
+    X.ovfFree = ws.ovfFree;
     {   // overflow slots (global), same structure
         char *g = (char *)ws.slotOvf;
         const size_t K1 = (size_t)k + 1;
         X.gm.s4 = (int4 *)g;               g += 16 * K1;
-        int32_t **f[9] = {&X.gm.key, &X.gm.id, &X.gm.g0, &X.gm.g1, &X.gm.ovf, &X.gm.rp, &X.gm.rn, &X.gm.cp, &X.gm.cn};
-        for (int u = 0; u < 9; ++u) { *f[u] = (int32_t *)g; g += 4 * K1; }
+        int32_t **f[5] = {&X.gm.key, &X.gm.id, &X.gm.g0, &X.gm.g1, &X.gm.ovf};
+        for (int u = 0; u < 5; ++u) { *f[u] = (int32_t *)g; g += 4 * K1; }
+        IX **fl[4] = {&X.gm.rp, &X.gm.rn, &X.gm.cp, &X.gm.cn};
+        for (int u = 0; u < 4; ++u) { *fl[u] = (IX *)g; g += sizeof(IX) * K1; }
         X.gm.t = (int16_t *)g;             g += 2 * K1;
         X.gm.legEnd = (int16_t *)g;        g += 2 * K1;
         X.gm.nsucc = (int16_t *)g;
     }
     for (int i = lane; i < slotCap; i += 32) { X.sm.key[i] = 0; X.sm.id[i] = INTMAX; X.freeStk[i] = (int16_t)(slotCap - 1 - i); }
     for (int i = lane; i < MAPN; i += 32) X.map[i] = -1;
-    for (int i = lane; i < 4 * m; i += 32) X.rowHead[i] = -1;
-    for (int i = lane; i < 4 * n; i += 32) X.colHead[i] = -1;
+    for (int i = lane; i < 4 * m; i += 32) X.rowHead[i] = (IX)-1;
+    for (int i = lane; i < 4 * n; i += 32) X.colHead[i] = (IX)-1;
     for (int i = lane; i < 2 * X.Wm; i += 32) X.rowBits[i] = 0u;
     for (int i = lane; i < 2 * X.Wn; i += 32) X.colBits[i] = 0u;
-    int freeTop = slotCap, ovfUsed = 0, hi = 0, err = 0;
+    int freeTop = slotCap, ovfFreeTop = 0, ovfUsed = 0, hi = 0, err = 0;
     __syncwarp();
 
     // moves without predecessors become statics
@@ -935,13 +959,13 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, const int *class
         int id = -1;
         int4 r = make_int4(0, 0, 0, 0), s4 = r;
         if (lane < cnt) { id = ready0[base + lane]; r = ws.rec[2 * id]; s4 = ws.rec[2 * id + 1]; }
-        const int si = alloc_slot(X, lane, cnt, freeTop, ovfUsed, hi, k, &err);
+        const int si = alloc_slot(X, lane, cnt, freeTop, ovfFreeTop, ovfUsed, hi, k, &err);
         int key = 0;
-        if (lane < cnt) key = fill_slot(X, si, id, r, s4);
+        if (lane < cnt && si >= 0) key = fill_slot(X, si, id, r, s4);
         __syncwarp();
         for (int u = 0; u < cnt; ++u) {
             const int su = __shfl_sync(FULL, si, u), ku = __shfl_sync(FULL, key, u);
-            if (lane == 0) { push_row(X, su, ku); push_col(X, su, ku); }
+            if (lane == 0 && su >= 0) { push_row(X, su, ku); push_col(X, su, ku); }
         }
         __syncwarp();
     }
@@ -996,10 +1020,10 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, const int *class
                 for (int p = h; p >= 0 && nc <= lineCap; p = chooseRow ? SLOTF(X, rn, p) : SLOTF(X, cn, p))
                     X.Kb[nc++] = ((long long)SLOTF(X, id, p) << 32) | (unsigned)p;
                 if (chooseRow) {
-                    X.rowHead[d * m + lr] = -1;
+                    X.rowHead[d * m + lr] = (IX)-1;
                     if (d < 2) atomicAnd(&X.rowBits[d * X.Wm + (lr >> 5)], ~(1u << (lr & 31)));
                 } else {
-                    X.colHead[d * n + lc] = -1;
+                    X.colHead[d * n + lc] = (IX)-1;
                     if (d >= 2) atomicAnd(&X.colBits[(d - 2) * X.Wn + (lc >> 5)], ~(1u << (lc & 31)));
                 }
             }
@@ -1141,14 +1165,14 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, const int *class
                     const unsigned bal = __ballot_sync(FULL, ready >= 0);
                     const int cnt = __popc(bal);
                     if (cnt) {
-                        const int ns_ = alloc_slot(X, __popc(bal & lt), cnt, freeTop, ovfUsed, hi, k, &err);
+                        const int ns_ = alloc_slot(X, __popc(bal & lt), cnt, freeTop, ovfFreeTop, ovfUsed, hi, k, &err);
                         int key = 0;
-                        if (ready >= 0) key = fill_slot(X, ns_, ready, r, s4);
+                        if (ready >= 0 && ns_ >= 0) key = fill_slot(X, ns_, ready, r, s4);
                         __syncwarp();
                         for (unsigned b = bal; b; b &= b - 1) {
                             const int w = __ffs(b) - 1;
                             const int sw = __shfl_sync(FULL, ns_, w), kw = __shfl_sync(FULL, key, w);
-                            if (lane == 0) { push_row(X, sw, kw); push_col(X, sw, kw); }
+                            if (lane == 0 && sw >= 0) { push_row(X, sw, kw); push_col(X, sw, kw); }
                         }
                     }
                     __syncwarp();
@@ -1161,10 +1185,12 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, const int *class
                 SLOTF(X, key, si) = 0;
                 SLOTF(X, id, si) = INTMAX;
             }
-            const bool recyc = fin && si < X.C;
-            const unsigned fb = __ballot_sync(FULL, recyc);
+            const bool recyc = fin && si < X.C, recycO = fin && si >= X.C;
+            const unsigned fb = __ballot_sync(FULL, recyc), fo = __ballot_sync(FULL, recycO);
             if (recyc) X.freeStk[freeTop + __popc(fb & lt)] = (int16_t)si;
+            if (recycO) X.ovfFree[ovfFreeTop + __popc(fo & lt)] = si;
             freeTop += __popc(fb);
+            ovfFreeTop += __popc(fo);
             __syncwarp();
         }
         for (int u = lane; u < nkeep; u += 32) { X.Mid[u] = (int)(X.Kb[u] >> 32); X.Msl[u] = (int)(X.Kb[u] & 0xffffffff); }
@@ -1215,3 +1241,17 @@ __global__ void k_sim(rr_instance *inst, JobWS *wsv, int count, const int *class
 }
 
 } // namespace rrk
+
+namespace rrk {
+// 16-bit slot links (sides up to 256) and 32-bit ones.
+__global__ void k_sim16(rr_instance *inst, JobWS *wsv, int count, const int *classList, const int *classCount,
+                        int slotCap, int lineCap)
+{
+    sim_body<int16_t>(inst, wsv, count, classList, classCount, slotCap, lineCap);
+}
+__global__ void k_sim32(rr_instance *inst, JobWS *wsv, int count, const int *classList, const int *classCount,
+                        int slotCap, int lineCap)
+{
+    sim_body<int32_t>(inst, wsv, count, classList, classCount, slotCap, lineCap);
+}
+}  // namespace rrk

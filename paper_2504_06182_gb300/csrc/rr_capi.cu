@@ -4,6 +4,7 @@
 #include <cstring>
 #include <cstdarg>
 #include <algorithm>
+#include <mutex>
 #include "rr_internal.cuh"
 
 namespace rrk {
@@ -30,15 +31,20 @@ __global__ void k_bsucc_scan(rr_instance *, JobWS *, int, Arena);
 __global__ void k_bsucc_fill(rr_instance *, JobWS *, int);
 __global__ void k_brec(rr_instance *, JobWS *, int);
 __global__ void k_classify(rr_instance *, int, int, const int *, int *, int *);
-__global__ void k_sim(rr_instance *, JobWS *, int, const int *, const int *, int, int);
+__global__ void k_sim16(rr_instance *, JobWS *, int, const int *, const int *, int, int);
+__global__ void k_sim32(rr_instance *, JobWS *, int, const int *, const int *, int, int);
 }  // namespace rrk
 
 using namespace rrk;
 
 static_assert(sizeof(rr_instance) == 128, "rr_instance layout is part of the ABI");
 
+// Kernels launched with more than the default 48 KB of dynamic shared memory.
+enum { SM_GSORT, SM_GSWEEP_H, SM_GSWEEP_V, SM_SIM16, SM_SIM32, SM_NKERNEL };
+
 struct rr_ctx {
     int device;
+    int smemLimit[SM_NKERNEL];   // dynamic shared memory each of those kernels may request
     char *arena;
     unsigned long long arena_size;
     unsigned long long *d_top;
@@ -87,6 +93,41 @@ static int fail(rr_ctx *ctx, int code, const char *fmt, ...)
         if (e_ != cudaSuccess) return fail(ctx, RR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+// Dynamic shared-memory limits are function attributes shared by every host
+// thread and every context of the process. They are set once per device, to
+// the device's opt-in maximum, before the first launch, and never changed:
+// setting them per launch would race with launches of the same kernels from
+// other threads (a server's worker next to a caller's own context), and a
+// lowered limit would break a launch that another thread already sized.
+static std::mutex g_limits_mu;
+static constexpr int MAX_DEVICES = 64;
+static bool g_limits_set[MAX_DEVICES];
+static int g_limits[MAX_DEVICES][SM_NKERNEL];
+
+static int smem_limits(int dev, int *out)
+{
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(nullptr, RR_ERR_CUDA, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_limits_mu);
+    if (!g_limits_set[dev]) {
+        int optin = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const void *fn[SM_NKERNEL] = {(const void *)k_gsort, (const void *)k_gsweep_h, (const void *)k_gsweep_v,
+                                      (const void *)k_sim16, (const void *)k_sim32};
+        for (int i = 0; e == cudaSuccess && i < SM_NKERNEL; ++i) {
+            cudaFuncAttributes fa;
+            e = cudaFuncGetAttributes(&fa, fn[i]);
+            if (e != cudaSuccess) break;
+            const int lim = optin - (int)fa.sharedSizeBytes;
+            e = cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+            g_limits[dev][i] = lim;
+        }
+        if (e != cudaSuccess) return fail(nullptr, RR_ERR_CUDA, "shared-memory limits: %s", cudaGetErrorString(e));
+        g_limits_set[dev] = true;
+    }
+    std::memcpy(out, g_limits[dev], sizeof(g_limits[dev]));
+    return RR_OK;
+}
+
 static int ensure_ws(rr_ctx *ctx, int count)
 {
     if (count <= ctx->ws_cap) return RR_OK;
@@ -124,7 +165,9 @@ extern "C" int rr_ctx_create(rr_ctx **out, int64_t arena_bytes)
         return RR_ERR_CUDA;
     }
     ctx->arena_size = (unsigned long long)arena_bytes;
-    int st = ensure_ws(ctx, 1);
+    int st = smem_limits(ctx->device, ctx->smemLimit);
+    if (st != RR_OK) { rr_ctx_destroy(ctx); return st; }
+    st = ensure_ws(ctx, 1);
     if (st != RR_OK) { rr_ctx_destroy(ctx); return st; }
     bool ok = cudaMalloc(&ctx->d_classSide, sizeof(int) * rr_ctx::NCLASS) == cudaSuccess &&
               cudaMalloc(&ctx->d_classCount, sizeof(int) * rr_ctx::NCLASS) == cudaSuccess &&
@@ -214,9 +257,9 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
         k_gfill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
         int P2 = 32;
         while (P2 < max_side) P2 <<= 1;
-        CUDA_TRY(cudaFuncSetAttribute(k_gsort, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 4 * P2));
-        CUDA_TRY(cudaFuncSetAttribute(k_gsweep_h, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 4 * max_side));
-        CUDA_TRY(cudaFuncSetAttribute(k_gsweep_v, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 8 * max_side));
+        if (8 * 4 * P2 > ctx->smemLimit[SM_GSORT] || 8 * 4 * max_side > ctx->smemLimit[SM_GSWEEP_H] ||
+            8 * 8 * max_side > ctx->smemLimit[SM_GSWEEP_V])
+            return fail(ctx, RR_ERR_ARG, "Gamma sweeps: shared memory for side %d too large", max_side);
         mark(ctx, s, "k_gsort");
         k_gsort<<<dim3(lineBlocks, count), 256, 8 * 4 * (size_t)P2, s>>>(d_inst, ctx->d_ws, count, P2);
         mark(ctx, s, "k_gsweep_h");
@@ -263,16 +306,25 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
         // ready moves never exceed two per column here (one chain head each
         // way); beyond the capacity slots spill to the global overflow area
         const int slotCap = 2 * side + 8, lineCap = side;
-        // per slot: s4 (16 B), nine int32 and four int16 fields; sort / merge
-        // buffer 2 (lineCap + 2) int64; id map; member ids and slots; successor
-        // buffer; static list heads [4][m] + [4][n]; pickup bitmaps
-        const size_t simSmem = 16ull * slotCap + 8ull * 2 * (lineCap + 2) + 4ull * 9 * slotCap + 2ull * 4 * slotCap +
-                               4ull * 512 + 4ull * 2 * (lineCap + 2) + 4ull * 512 + 4ull * 8 * lineCap +
-                               4ull * 4 * ((lineCap + 31) / 32) + 64;
-        if (simSmem > 227 * 1024) return fail(ctx, RR_ERR_ARG, "simulation shared memory %zu too large", simSmem);
-        CUDA_TRY(cudaFuncSetAttribute(k_sim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)simSmem));
-        k_sim<<<count, 32, simSmem, cs>>>(d_inst, ctx->d_ws, count, ctx->d_classList + (size_t)c * count,
-                                         ctx->d_classCount + c, slotCap, lineCap);
+        // per slot: s4 (16 B), five int32 fields, four links, four int16
+        // fields; sort / merge buffer 2 (lineCap + 2) int64; id map; member ids
+        // and slots; successor buffer; pickup bitmaps; static list heads
+        // [4][m] + [4][n]. Links are 16-bit up to side 256 (a ready set there
+        // stays below 32 768 moves: ready moves are vertex-disjoint).
+        const bool narrow = lineCap <= 256;
+        const size_t ix = narrow ? 2 : 4;
+        const size_t simSmem = 16ull * slotCap + 8ull * 2 * (lineCap + 2) +
+                               4ull * (5 * slotCap + 512 + 2 * (lineCap + 2) + 512 + 4 * ((lineCap + 31) / 32)) +
+                               ix * (4ull * slotCap + 8ull * lineCap) + 2ull * 4 * slotCap + 64;
+        if (simSmem > (size_t)ctx->smemLimit[narrow ? SM_SIM16 : SM_SIM32])
+            return fail(ctx, RR_ERR_ARG, "simulation shared memory %zu too large", simSmem);
+        if (narrow) {
+            k_sim16<<<count, 32, simSmem, cs>>>(d_inst, ctx->d_ws, count, ctx->d_classList + (size_t)c * count,
+                                                      ctx->d_classCount + c, slotCap, lineCap);
+        } else {
+            k_sim32<<<count, 32, simSmem, cs>>>(d_inst, ctx->d_ws, count, ctx->d_classList + (size_t)c * count,
+                                                      ctx->d_classCount + c, slotCap, lineCap);
+        }
         CUDA_TRY(cudaEventRecord(ctx->evJoin[c], cs));
         CUDA_TRY(cudaStreamWaitEvent(s, ctx->evJoin[c], 0));
     }

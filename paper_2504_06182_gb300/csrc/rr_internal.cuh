@@ -85,6 +85,7 @@ struct JobWS {
     int32_t *firstH;       // m * n: lowest-id L-move crossing each vertex, -1
     int32_t genericGamma;  // set when the sweep order does not hold: per-vertex lists instead
     void *slotOvf;         // k simulation slots beyond the shared-memory ones
+    int32_t *ovfFree;      // k: recycled overflow slots
 };
 
 // Successor entries carry this flag when the successor has a single
