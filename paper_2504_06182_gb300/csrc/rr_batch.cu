@@ -20,6 +20,7 @@
 // d) or column (horizontal d) reaches a waiting ready move of direction d.
 // Between such events every batch is the same, so runs of identical batches
 // are written in one go.
+#include <type_traits>
 #include "rr_internal.cuh"
 
 namespace rrk {
@@ -133,7 +134,7 @@ __global__ void k_bsetup(rr_instance *inst, JobWS *wsv, int count, Arena A)
             ws.rec = (int4 *)arena_alloc(A, 32ull * (k + 1), &ok);   // record, successors: one 32 B sector
             ws.succ4 = ws.rec + 1;
             ws.ready0 = (int32_t *)arena_alloc(A, 4ull * (k + 1) + 16, &ok);
-            ws.slotOvf = arena_alloc(A, 64ull * (k + 1), &ok);
+            ws.slotOvf = arena_alloc(A, 40ull * (k + 1), &ok);
             ws.ovfFree = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
             ws.succ = nullptr; ws.E = 0;
             if (!ok) I->status = RR_ERR_WORKSPACE;
@@ -604,8 +605,6 @@ __global__ void k_brec(rr_instance *inst, JobWS *wsv, int count)
 // batch is dissolved back into the lists only when the leader's line or
 // direction no longer matches the members'.
 
-constexpr int MAPN = 512;       // id -> slot cache for finding the next leader
-constexpr int SBUF = 512;       // successor entries released per round
 constexpr int KEY_LIVE = 1 << 22;
 constexpr int KEY_MEM = 1 << 23;
 constexpr int INTMAX = 0x7fffffff;
@@ -616,10 +615,9 @@ template <typename IX> struct SlotSoA {
     int32_t *g0, *g1; // src_row | src_col << 16, dst_row | dst_col << 16
     int16_t *t;       // elementary steps done (paths are shorter than 2 048 steps)
     int16_t *legEnd;  // t at the end of the current straight leg
-    int16_t *nsucc;
-    int32_t *ovf;
     IX *rp, *rn, *cp, *cn;        // static-list links (slot indices, -1)
-    int4 *s4;         // first four successors
+    // a move's successors are read from its record when it finishes: only
+    // the leader and the members ever finish
 };
 
 template <typename IX> struct Sim {
@@ -635,7 +633,21 @@ template <typename IX> struct Sim {
     int32_t *sbuf;
 };
 
-#define SLOTF(X, f, i) (*((i) < (X).C ? &(X).sm.f[(i)] : &(X).gm.f[(i) - (X).C]))
+// A slot field: shared memory below the capacity C, the global overflow area
+// above it. Loads and stores branch on the index (rather than selecting a
+// pointer) so that the common shared-memory case stays a shared access.
+template <typename T> struct SlotRef {
+    T *s, *g;
+    int i, C;
+    __device__ __forceinline__ operator T() const { return i < C ? s[i] : g[i - C]; }
+    __device__ __forceinline__ SlotRef &operator=(T v)
+    {
+        if (i < C) s[i] = v; else g[i - C] = v;
+        return *this;
+    }
+};
+#define SLOTF(X, f, i) \
+    (SlotRef<std::remove_reference_t<decltype(*(X).sm.f)>>{(X).sm.f, (X).gm.f, (int)(i), (X).C})
 
 __device__ __forceinline__ int key_of(int r, int c, int d) { return r | (c << 10) | (d << 20) | KEY_LIVE; }
 __device__ __forceinline__ int key_r(int k) { return k & 1023; }
@@ -706,15 +718,22 @@ __device__ void unlink_col(const Sim<IX> &X, int si, int key)
     if (*h < 0 && key_d(key) >= 2) atomicAnd(&X.colBits[(key_d(key) - 2) * X.Wn + (key_c(key) >> 5)], ~(1u << (key_c(key) & 31)));
 }
 
-// First i in 1..maxq with bit (pos + i*delta) set, or 0.
+// First i in 1..maxq with bit (pos + i*delta) set, or 0 (delta = +-1): a
+// word at a time, the nearest set bit found with ffs / clz.
 __device__ int bit_scan(const uint32_t *b, int limit, int pos, int delta, int maxq)
 {
-    for (int i = 1; i <= maxq; ++i) {
-        const int x = pos + i * delta;
-        if (x < 0 || x >= limit) return 0;
-        const uint32_t w = b[x >> 5];
-        if (w == 0u) { i = delta > 0 ? ((x | 31) - pos) : (pos - (x & ~31)); continue; }
-        if ((w >> (x & 31)) & 1u) return i;
+    if (delta > 0) {
+        const int end = min(limit - 1, pos + maxq);
+        for (int x = pos + 1; x <= end; x = (x | 31) + 1) {
+            const uint32_t w = b[x >> 5] & (~0u << (x & 31));
+            if (w) { const int y = (x & ~31) + __ffs(w) - 1; return y <= end ? y - pos : 0; }
+        }
+    } else {
+        const int end = max(0, pos - maxq);
+        for (int x = pos - 1; x >= end; x = (x & ~31) - 1) {
+            const uint32_t w = b[x >> 5] & (0xffffffffu >> (31 - (x & 31)));
+            if (w) { const int y = (x & ~31) + 31 - __clz(w); return y >= end ? pos - y : 0; }
+        }
     }
     return 0;
 }
@@ -807,7 +826,7 @@ __device__ __forceinline__ int alloc_slot(const Sim<IX> &X, int rank, int cnt, i
 
 // A newly ready move: fill its slot (the caller links it into the lists).
 template <typename IX>
-__device__ __forceinline__ int fill_slot(const Sim<IX> &X, int si, int id, int4 r, int4 s4)
+__device__ __forceinline__ int fill_slot(const Sim<IX> &X, int si, int id, int4 r)
 {
     int rr, cc, d, rem, len;
     move_pos(r.x, r.y, 0, &rr, &cc, &d, &rem, &len);
@@ -818,11 +837,14 @@ __device__ __forceinline__ int fill_slot(const Sim<IX> &X, int si, int id, int4 
     SLOTF(X, g1, si) = r.y;
     SLOTF(X, t, si) = 0;
     SLOTF(X, legEnd, si) = (int16_t)rem;
-    SLOTF(X, nsucc, si) = (int16_t)r.z;
-    SLOTF(X, ovf, si) = r.w;
-    SLOTF(X, s4, si) = s4;
     X.map[id & (MAPN - 1)] = si;
     return key;
+}
+
+// Pull a move's own record toward L1: it is read when the move finishes.
+__device__ __forceinline__ void prefetch_rec(const JobWS &ws, int id)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(ws.rec + 2 * id));
 }
 
 // Pull the records of a move's first successors toward L1: they are read when
@@ -903,14 +925,12 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
     Sim<IX> X;
     X.C = slotCap; X.m = m; X.n = n; X.Wm = (m + 31) >> 5; X.Wn = (n + 31) >> 5;
     const int lbuf = 2 * (lineCap + 2);
-    X.sm.s4 = smem_i4;
-    X.Kb = (long long *)(X.sm.s4 + slotCap);
+    X.Kb = (long long *)smem_i4;
     int32_t *p32 = (int32_t *)(X.Kb + lbuf);
     X.sm.key = p32; p32 += slotCap;
     X.sm.id = p32; p32 += slotCap;
     X.sm.g0 = p32; p32 += slotCap;
     X.sm.g1 = p32; p32 += slotCap;
-    X.sm.ovf = p32; p32 += slotCap;
     X.map = p32; p32 += MAPN;
     X.Mid = p32; p32 += lineCap + 2;
     X.Msl = p32; p32 += lineCap + 2;
@@ -927,20 +947,17 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
     int16_t *p16 = (int16_t *)pix;
     X.sm.t = p16; p16 += slotCap;
     X.sm.legEnd = p16; p16 += slotCap;
-    X.sm.nsucc = p16; p16 += slotCap;
     X.freeStk = p16;
     X.ovfFree = ws.ovfFree;
     {   // overflow slots (global), same structure
         char *g = (char *)ws.slotOvf;
         const size_t K1 = (size_t)k + 1;
-        X.gm.s4 = (int4 *)g;               g += 16 * K1;
-        int32_t **f[5] = {&X.gm.key, &X.gm.id, &X.gm.g0, &X.gm.g1, &X.gm.ovf};
-        for (int u = 0; u < 5; ++u) { *f[u] = (int32_t *)g; g += 4 * K1; }
+        int32_t **f[4] = {&X.gm.key, &X.gm.id, &X.gm.g0, &X.gm.g1};
+        for (int u = 0; u < 4; ++u) { *f[u] = (int32_t *)g; g += 4 * K1; }
         IX **fl[4] = {&X.gm.rp, &X.gm.rn, &X.gm.cp, &X.gm.cn};
         for (int u = 0; u < 4; ++u) { *fl[u] = (IX *)g; g += sizeof(IX) * K1; }
         X.gm.t = (int16_t *)g;             g += 2 * K1;
-        X.gm.legEnd = (int16_t *)g;        g += 2 * K1;
-        X.gm.nsucc = (int16_t *)g;
+        X.gm.legEnd = (int16_t *)g;
     }
     for (int i = lane; i < slotCap; i += 32) { X.sm.key[i] = 0; X.sm.id[i] = INTMAX; X.freeStk[i] = (int16_t)(slotCap - 1 - i); }
     for (int i = lane; i < MAPN; i += 32) X.map[i] = -1;
@@ -957,11 +974,11 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
     for (int base = 0; base < nready0; base += 32) {
         const int cnt = min(32, nready0 - base);
         int id = -1;
-        int4 r = make_int4(0, 0, 0, 0), s4 = r;
-        if (lane < cnt) { id = ready0[base + lane]; r = ws.rec[2 * id]; s4 = ws.rec[2 * id + 1]; }
+        int4 r = make_int4(0, 0, 0, 0);
+        if (lane < cnt) { id = ready0[base + lane]; r = ws.rec[2 * id]; }
         const int si = alloc_slot(X, lane, cnt, freeTop, ovfFreeTop, ovfUsed, hi, k, &err);
         int key = 0;
-        if (lane < cnt && si >= 0) key = fill_slot(X, si, id, r, s4);
+        if (lane < cnt && si >= 0) key = fill_slot(X, si, id, r);
         __syncwarp();
         for (int u = 0; u < cnt; ++u) {
             const int su = __shfl_sync(FULL, si, u), ku = __shfl_sync(FULL, key, u);
@@ -1010,6 +1027,10 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
         err = __shfl_sync(FULL, err, 0);
         if (err) break;
         if (nm > 0) { if (rowLine) minA = min(minA, X.Mid[0]); else minB = min(minB, X.Mid[0]); }
+        // records of up to 32 newcomers: fetched when they join, their
+        // successors' records prefetched once the segment is emitted
+        int4 nrec = make_int4(0, 0, 0, 0), ns4 = nrec;
+        int npref = 0;
         if (minA != INTMAX || minB != INTMAX) {
             const bool chooseRow = minA < minB;
             if (nm > 0 && chooseRow != rowLine) { dissolve(X, nm, rowLine); nm = 0; }
@@ -1036,33 +1057,57 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
                 const int key = SLOTF(X, key, si);
                 if (chooseRow) unlink_col(X, si, key); else unlink_row(X, si, key);
                 SLOTF(X, key, si) = key | KEY_MEM;
-                prefetch_succ(ws, SLOTF(X, s4, si), SLOTF(X, nsucc, si));
+                const int id = (int)(X.Kb[u] >> 32);
+                if (u < 32) { nrec = ws.rec[2 * id]; ns4 = ws.rec[2 * id + 1]; }
+                else prefetch_rec(ws, id);
             }
             __syncwarp();
-            warp_sort64(X.Kb, nc);
-            // merge the sorted newcomers into the sorted members
+            // merge the newcomers into the sorted members (keys id << 32 | slot)
             if (nc > 0) {
                 const int tot = nm + nc;
                 long long *out = X.Kb + (lineCap + 2);
-                for (int u = lane; u < nm; u += 32) {          // member u: rank among newcomers
-                    const long long key = ((long long)X.Mid[u] << 32) | (unsigned)X.Msl[u];
-                    int lo = 0, hi2 = nc;
-                    while (lo < hi2) { const int md = (lo + hi2) >> 1; if (X.Kb[md] < key) lo = md + 1; else hi2 = md; }
-                    out[u + lo] = key;
-                }
-                for (int u = lane; u < nc; u += 32) {          // newcomer u: rank among members
-                    const long long key = X.Kb[u];
-                    int lo = 0, hi2 = nm;
-                    while (lo < hi2) {
-                        const int md = (lo + hi2) >> 1;
-                        if ((((long long)X.Mid[md] << 32) | (unsigned)X.Msl[md]) < key) lo = md + 1; else hi2 = md;
+                if (nc <= 32) {
+                    // few newcomers (the usual case): ranks by counting
+                    for (int u = lane; u < nm; u += 32) {
+                        const long long key = ((long long)X.Mid[u] << 32) | (unsigned)X.Msl[u];
+                        int r = 0;
+                        for (int j = 0; j < nc; ++j) r += X.Kb[j] < key;
+                        out[u + r] = key;
                     }
-                    out[u + lo] = key;
+                    if (lane < nc) {
+                        const long long key = X.Kb[lane];
+                        int r = 0;
+                        for (int j = 0; j < nc; ++j) r += X.Kb[j] < key;
+                        int lo = 0, hi2 = nm;
+                        while (lo < hi2) {
+                            const int md = (lo + hi2) >> 1;
+                            if ((((long long)X.Mid[md] << 32) | (unsigned)X.Msl[md]) < key) lo = md + 1; else hi2 = md;
+                        }
+                        out[r + lo] = key;
+                    }
+                } else {
+                    warp_sort64(X.Kb, nc);
+                    for (int u = lane; u < nm; u += 32) {      // member u: rank among newcomers
+                        const long long key = ((long long)X.Mid[u] << 32) | (unsigned)X.Msl[u];
+                        int lo = 0, hi2 = nc;
+                        while (lo < hi2) { const int md = (lo + hi2) >> 1; if (X.Kb[md] < key) lo = md + 1; else hi2 = md; }
+                        out[u + lo] = key;
+                    }
+                    for (int u = lane; u < nc; u += 32) {      // newcomer u: rank among members
+                        const long long key = X.Kb[u];
+                        int lo = 0, hi2 = nm;
+                        while (lo < hi2) {
+                            const int md = (lo + hi2) >> 1;
+                            if ((((long long)X.Mid[md] << 32) | (unsigned)X.Msl[md]) < key) lo = md + 1; else hi2 = md;
+                        }
+                        out[u + lo] = key;
+                    }
                 }
                 __syncwarp();
                 for (int u = lane; u < tot; u += 32) { X.Mid[u] = (int)(out[u] >> 32); X.Msl[u] = (int)(out[u] & 0xffffffff); }
                 nm = tot;
             }
+            npref = min(nc, 32);
             rowLine = chooseRow;
             lineIdx = chooseRow ? lr : lc;
             dm = d;
@@ -1105,11 +1150,13 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
         // advance: u = 0 is the leader, u >= 1 member u-1. Finished moves
         // release their successors; members whose leg ended leave the batch
         // and become statics; the others stay members.
+        if (lane < npref) prefetch_succ(ws, ns4, nrec.z);
         int leaderDone = 0, nkeep = 0;
         for (int u0 = 0; u0 < ns; u0 += 32) {
             const int u = u0 + lane;
             bool fin = false, turn = false, act = u < ns;
-            int si = -1, nsu = 0, newKey = 0;
+            int si = -1, nsu = 0, newKey = 0, ov = 0;
+            int4 fs4 = make_int4(0, 0, 0, 0);
             if (act) {
                 si = u == 0 ? Ls : X.Msl[u - 1];
                 const int t = SLOTF(X, t, si) + kseg;
@@ -1117,8 +1164,13 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
                 move_pos(SLOTF(X, g0, si), SLOTF(X, g1, si), t, &r_, &c_, &d_, &rem, &len);
                 SLOTF(X, t, si) = (int16_t)t;
                 fin = t >= len;
-                if (fin) nsu = SLOTF(X, nsucc, si);
-                else {
+                if (fin) {
+                    const int id = SLOTF(X, id, si);
+                    const int4 own = ws.rec[2 * id];
+                    fs4 = ws.rec[2 * id + 1];
+                    nsu = own.z;
+                    ov = own.w;
+                } else {
                     turn = u > 0 && d_ != d;
                     newKey = key_of(r_, c_, d_) | (u > 0 && !turn ? KEY_MEM : 0);
                     SLOTF(X, key, si) = newKey;
@@ -1144,22 +1196,20 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
             const int total = __shfl_sync(FULL, off + nsu, 31);
             for (int base = 0; base < total; base += SBUF) {
                 if (fin) {
-                    const int4 s4 = SLOTF(X, s4, si);
-                    const int ov = SLOTF(X, ovf, si);
                     for (int e = max(0, base - off); e < nsu && off + e < base + SBUF; ++e)
-                        X.sbuf[off + e - base] = e == 0 ? s4.x : e == 1 ? s4.y : e == 2 ? s4.z : e == 3 ? s4.w
-                                                                                              : ~(ov + e - 4);
+                        X.sbuf[off + e - base] = e == 0 ? fs4.x : e == 1 ? fs4.y : e == 2 ? fs4.z : e == 3 ? fs4.w
+                                                                                                : ~(ov + e - 4);
                 }
                 __syncwarp();
                 const int nb = min(SBUF, total - base);
                 for (int b0 = 0; b0 < nb; b0 += 32) {
                     int ready = -1;
-                    int4 r = make_int4(0, 0, 0, 0), s4 = r;
+                    int4 r = make_int4(0, 0, 0, 0);
                     if (b0 + lane < nb) {
                         int32_t e = X.sbuf[b0 + lane];
                         if (e < 0) e = ws.succ[~e];
                         const int id = e & SUCC_ID;
-                        r = ws.rec[2 * id]; s4 = ws.rec[2 * id + 1];   // fetched with the counter update
+                        r = ws.rec[2 * id];   // fetched with the counter update
                         if ((e & SUCC_SINGLE) || atomicSub(&ws.indeg[id], 1) == 1) ready = id;
                     }
                     const unsigned bal = __ballot_sync(FULL, ready >= 0);
@@ -1167,7 +1217,7 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
                     if (cnt) {
                         const int ns_ = alloc_slot(X, __popc(bal & lt), cnt, freeTop, ovfFreeTop, ovfUsed, hi, k, &err);
                         int key = 0;
-                        if (ready >= 0 && ns_ >= 0) key = fill_slot(X, ns_, ready, r, s4);
+                        if (ready >= 0 && ns_ >= 0) key = fill_slot(X, ns_, ready, r);
                         __syncwarp();
                         for (unsigned b = bal; b; b &= b - 1) {
                             const int w = __ffs(b) - 1;
@@ -1213,7 +1263,7 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
             else {
                 Ls = cand;
                 L = SLOTF(X, id, Ls);
-                if (lane == 0) prefetch_succ(ws, SLOTF(X, s4, Ls), SLOTF(X, nsucc, Ls));
+                if (lane == 0) prefetch_rec(ws, L);
                 const int kk = SLOTF(X, key, Ls);
                 if (kk & KEY_MEM) {
                     if (nm == 0 || X.Msl[0] != Ls) { err = RR_ERR_INTERNAL; break; }

@@ -306,16 +306,11 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
         // ready moves never exceed two per column here (one chain head each
         // way); beyond the capacity slots spill to the global overflow area
         const int slotCap = 2 * side + 8, lineCap = side;
-        // per slot: s4 (16 B), five int32 fields, four links, four int16
-        // fields; sort / merge buffer 2 (lineCap + 2) int64; id map; member ids
-        // and slots; successor buffer; pickup bitmaps; static list heads
-        // [4][m] + [4][n]. Links are 16-bit up to side 256 (a ready set there
-        // stays below 32 768 moves: ready moves are vertex-disjoint).
+        // links are 16-bit up to side 256: about 2 * side moves are ready at
+        // once, far below 32 768; an instance that would need more slots
+        // ends with an internal error instead of wrapping an index
         const bool narrow = lineCap <= 256;
-        const size_t ix = narrow ? 2 : 4;
-        const size_t simSmem = 16ull * slotCap + 8ull * 2 * (lineCap + 2) +
-                               4ull * (5 * slotCap + 512 + 2 * (lineCap + 2) + 512 + 4 * ((lineCap + 31) / 32)) +
-                               ix * (4ull * slotCap + 8ull * lineCap) + 2ull * 4 * slotCap + 64;
+        const size_t simSmem = sim_smem_bytes(slotCap, lineCap, narrow ? 2 : 4);
         if (simSmem > (size_t)ctx->smemLimit[narrow ? SM_SIM16 : SM_SIM32])
             return fail(ctx, RR_ERR_ARG, "simulation shared memory %zu too large", simSmem);
         if (narrow) {

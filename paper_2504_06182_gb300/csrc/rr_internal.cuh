@@ -88,6 +88,22 @@ struct JobWS {
     int32_t *ovfFree;      // k: recycled overflow slots
 };
 
+// Shared memory of one batching-simulation block (one warp, one instance):
+// sort / merge buffer, slot table, id map, members, successor buffer,
+// pickup bitmaps, list links and heads (ix bytes each), step counters and
+// the free-slot stack. The kernel's layout follows this order.
+constexpr int MAPN = 256;       // id -> slot cache for finding the next leader
+constexpr int SBUF = 256;       // successor entries released per round
+__host__ __device__ inline size_t sim_smem_bytes(int slotCap, int lineCap, int ix)
+{
+    const size_t S = (size_t)slotCap, L = (size_t)lineCap;
+    return 8 * 2 * (L + 2) +                                            // Kb
+           4 * (4 * S + MAPN + 2 * (L + 2) + SBUF + 4 * ((L + 31) / 32)) +  // key id g0 g1, map, Mid Msl, sbuf, bits
+           (size_t)ix * (4 * S + 8 * L) +                                // rp rn cp cn, row and column heads
+           2 * 3 * S +                                                   // t, legEnd, free stack
+           64;
+}
+
 // Successor entries carry this flag when the successor has a single
 // predecessor: it becomes ready as soon as that predecessor finishes.
 constexpr int32_t SUCC_SINGLE = 1 << 30;
