@@ -129,14 +129,16 @@ __global__ void k_bsetup(rr_instance *inst, JobWS *wsv, int count, Arena A)
             ws.rowCur = (int32_t *)arena_alloc(A, 4ull * (m + 1), &ok);
             ws.rowList = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
             ws.firstH = (int32_t *)arena_alloc(A, 4ull * cells, &ok);
-            ws.succOff = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
+            ws.succCnt = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
             ws.indeg = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
             ws.rec = (int4 *)arena_alloc(A, 32ull * (k + 1), &ok);   // record, successors: one 32 B sector
             ws.succ4 = ws.rec + 1;
             ws.ready0 = (int32_t *)arena_alloc(A, 4ull * (k + 1) + 16, &ok);
             ws.slotOvf = arena_alloc(A, 40ull * (k + 1), &ok);
             ws.ovfFree = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
-            ws.succ = nullptr; ws.E = 0;
+            // a path has at most as many distinct successors as vertices: they
+            // are stored at the path's vertex offset, so no count pass or scan
+            ws.succ = (int32_t *)arena_alloc(A, 4ull * (tp + 1), &ok);
             if (!ok) I->status = RR_ERR_WORKSPACE;
         }
     }
@@ -507,7 +509,9 @@ __device__ int distinct_succ(const int32_t *seq, int len, Emit emit)
     return cnt;
 }
 
-__global__ void k_bsucc_count(rr_instance *inst, JobWS *wsv, int count)
+// Distinct successors of every path, written at the path's vertex offset,
+// their count, and the in-degree of every successor.
+__global__ void k_bsucc(rr_instance *inst, JobWS *wsv, int count)
 {
     const int q = blockIdx.y;
     if (q >= count) return;
@@ -515,44 +519,11 @@ __global__ void k_bsucc_count(rr_instance *inst, JobWS *wsv, int count)
     if (!live(I)) return;
     JobWS &ws = wsv[q];
     const int64_t k = I->n_moves;
+    int32_t *indeg = ws.indeg;
     for (int64_t b = blockIdx.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)gridDim.x * blockDim.x) {
         const int lo = ws.pairOff[b], hi = ws.pairOff[b + 1];
-        ws.succOff[b] = distinct_succ(ws.nextAt + lo, hi - lo, [](int, int32_t) {});
-    }
-}
-
-__global__ void k_bsucc_scan(rr_instance *inst, JobWS *wsv, int count, Arena A)
-{
-    __shared__ long long s_tmp[34];
-    const int q = blockIdx.x;
-    if (q >= count) return;
-    rr_instance *I = &inst[q];
-    if (!live(I)) return;
-    JobWS &ws = wsv[q];
-    const int k = (int)I->n_moves;
-    const long long E = block_exclusive_scan(ws.succOff, k, s_tmp);
-    if (threadIdx.x == 0) {
-        ws.succOff[k] = (int32_t)E;
-        ws.E = E;
-        bool ok = true;
-        ws.succ = (int32_t *)arena_alloc(A, 4ull * (E + 1), &ok);
-        if (!ok) I->status = RR_ERR_WORKSPACE;
-    }
-}
-
-__global__ void k_bsucc_fill(rr_instance *inst, JobWS *wsv, int count)
-{
-    const int q = blockIdx.y;
-    if (q >= count) return;
-    const rr_instance *I = &inst[q];
-    if (!live(I)) return;
-    JobWS &ws = wsv[q];
-    const int64_t k = I->n_moves;
-    for (int64_t b = blockIdx.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)gridDim.x * blockDim.x) {
-        const int lo = ws.pairOff[b], hi = ws.pairOff[b + 1];
-        int32_t *out = ws.succ + ws.succOff[b];
-        int32_t *indeg = ws.indeg;
-        distinct_succ(ws.nextAt + lo, hi - lo, [&](int u, int32_t s) { out[u] = s; atomicAdd(&indeg[s], 1); });
+        int32_t *out = ws.succ + lo;
+        ws.succCnt[b] = distinct_succ(ws.nextAt + lo, hi - lo, [&](int u, int32_t s) { out[u] = s; atomicAdd(&indeg[s], 1); });
     }
 }
 
@@ -570,7 +541,7 @@ __global__ void k_brec(rr_instance *inst, JobWS *wsv, int count)
     const int64_t k = I->n_moves;
     for (int64_t b = blockIdx.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)gridDim.x * blockDim.x) {
         const rr_move p = I->moves[b];
-        const int lo = ws.succOff[b], hi = ws.succOff[b + 1];
+        const int lo = ws.pairOff[b], hi = lo + ws.succCnt[b];
         int4 r;
         r.x = (p.src_row & 0xffff) | (p.src_col << 16);
         r.y = (p.dst_row & 0xffff) | (p.dst_col << 16);
@@ -718,6 +689,35 @@ __device__ void unlink_col(const Sim<IX> &X, int si, int key)
     if (*h < 0 && key_d(key) >= 2) atomicAnd(&X.colBits[(key_d(key) - 2) * X.Wn + (key_c(key) >> 5)], ~(1u << (key_c(key) & 31)));
 }
 
+// Link a slot into its row list and its column list (both head loads first:
+// the two lists are independent).
+template <typename IX>
+__device__ __forceinline__ void push_both(const Sim<IX> &X, int si, int key)
+{
+    IX *hr = &X.rowHead[key_d(key) * X.m + key_r(key)];
+    IX *hc = &X.colHead[key_d(key) * X.n + key_c(key)];
+    const int oldR = *hr, oldC = *hc;
+    SLOTF(X, rp, si) = (IX)-1; SLOTF(X, rn, si) = (IX)oldR;
+    SLOTF(X, cp, si) = (IX)-1; SLOTF(X, cn, si) = (IX)oldC;
+    if (oldR >= 0) SLOTF(X, rp, oldR) = (IX)si;
+    if (oldC >= 0) SLOTF(X, cp, oldC) = (IX)si;
+    *hr = (IX)si;
+    *hc = (IX)si;
+    if (key_d(key) < 2) atomicOr(&X.rowBits[key_d(key) * X.Wm + (key_r(key) >> 5)], 1u << (key_r(key) & 31));
+    else atomicOr(&X.colBits[(key_d(key) - 2) * X.Wn + (key_c(key) >> 5)], 1u << (key_c(key) & 31));
+}
+// Lanes in `pend` link their slots, one lane at a time (two of them may
+// share a list).
+template <typename IX>
+__device__ __forceinline__ void push_lanes(const Sim<IX> &X, unsigned pend, int si, int key)
+{
+    const int lane = threadIdx.x & 31;
+    for (; pend; pend &= pend - 1) {
+        if (lane == __ffs(pend) - 1) push_both(X, si, key);
+        __syncwarp();
+    }
+}
+
 // First i in 1..maxq with bit (pos + i*delta) set, or 0 (delta = +-1): a
 // word at a time, the nearest set bit found with ffs / clz.
 __device__ int bit_scan(const uint32_t *b, int limit, int pos, int delta, int maxq)
@@ -817,10 +817,7 @@ __device__ __forceinline__ int alloc_slot(const Sim<IX> &X, int rank, int cnt, i
     const int lastOk = min(X.C + kmax, sizeof(IX) == 2 ? 32767 : 0x7fffffff);
     if (si > lastOk) si = -1;
     if (ovfUsed > kmax || X.C + ovfUsed > lastOk + 1) *err = RR_ERR_INTERNAL;
-    int top = si + 1;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) top = max(top, __shfl_xor_sync(FULL, top, o));
-    hi = max(hi, top);
+    hi = X.C + ovfUsed;            // every slot ever used lies below
     return si;
 }
 
@@ -965,7 +962,7 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
     for (int i = lane; i < 4 * n; i += 32) X.colHead[i] = (IX)-1;
     for (int i = lane; i < 2 * X.Wm; i += 32) X.rowBits[i] = 0u;
     for (int i = lane; i < 2 * X.Wn; i += 32) X.colBits[i] = 0u;
-    int freeTop = slotCap, ovfFreeTop = 0, ovfUsed = 0, hi = 0, err = 0;
+    int freeTop = slotCap, ovfFreeTop = 0, ovfUsed = 0, hi = slotCap, err = 0;
     __syncwarp();
 
     // moves without predecessors become statics
@@ -980,11 +977,7 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
         int key = 0;
         if (lane < cnt && si >= 0) key = fill_slot(X, si, id, r);
         __syncwarp();
-        for (int u = 0; u < cnt; ++u) {
-            const int su = __shfl_sync(FULL, si, u), ku = __shfl_sync(FULL, key, u);
-            if (lane == 0 && su >= 0) { push_row(X, su, ku); push_col(X, su, ku); }
-        }
-        __syncwarp();
+        push_lanes(X, __ballot_sync(FULL, lane < cnt && si >= 0), si, key);
     }
 
     const int64_t cap_ops = I->cap_ops, cap_mem = I->cap_members;
@@ -1183,14 +1176,8 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
             const unsigned kb = __ballot_sync(FULL, keep);
             if (keep) X.Kb[nkeep + __popc(kb & lt)] = ((long long)X.Mid[u - 1] << 32) | (unsigned)si;
             nkeep += __popc(kb);
-            // members whose leg ended become statics (lane 0, in order)
-            const unsigned tb = __ballot_sync(FULL, turn);
-            for (unsigned b = tb; b; b &= b - 1) {
-                const int w = __ffs(b) - 1;
-                const int sw = __shfl_sync(FULL, si, w), kw = __shfl_sync(FULL, newKey, w);
-                if (lane == 0) { push_row(X, sw, kw); push_col(X, sw, kw); }
-            }
-            __syncwarp();
+            // members whose leg ended become statics
+            push_lanes(X, __ballot_sync(FULL, turn), si, newKey);
             // successor entries of the finished moves, in rounds of SBUF
             const int off = warp_incl_scan(nsu) - nsu;
             const int total = __shfl_sync(FULL, off + nsu, 31);
@@ -1219,11 +1206,7 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
                         int key = 0;
                         if (ready >= 0 && ns_ >= 0) key = fill_slot(X, ns_, ready, r);
                         __syncwarp();
-                        for (unsigned b = bal; b; b &= b - 1) {
-                            const int w = __ffs(b) - 1;
-                            const int sw = __shfl_sync(FULL, ns_, w), kw = __shfl_sync(FULL, key, w);
-                            if (lane == 0 && sw >= 0) { push_row(X, sw, kw); push_col(X, sw, kw); }
-                        }
+                        push_lanes(X, __ballot_sync(FULL, ready >= 0 && ns_ >= 0), ns_, key);
                     }
                     __syncwarp();
                 }

@@ -26,9 +26,7 @@ __global__ void k_bcount(rr_instance *, JobWS *, int);
 __global__ void k_bscan_cells(rr_instance *, JobWS *, int);
 __global__ void k_bfill(rr_instance *, JobWS *, int);
 __global__ void k_bsort(rr_instance *, JobWS *, int);
-__global__ void k_bsucc_count(rr_instance *, JobWS *, int);
-__global__ void k_bsucc_scan(rr_instance *, JobWS *, int, Arena);
-__global__ void k_bsucc_fill(rr_instance *, JobWS *, int);
+__global__ void k_bsucc(rr_instance *, JobWS *, int);
 __global__ void k_brec(rr_instance *, JobWS *, int);
 __global__ void k_classify(rr_instance *, int, int, const int *, int *, int *);
 __global__ void k_sim16(rr_instance *, JobWS *, int, const int *, const int *, int, int);
@@ -277,12 +275,8 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
     k_bfill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
     mark(ctx, s, "k_bsort");
     k_bsort<<<dim3(cellBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
-    mark(ctx, s, "k_bsucc_count");
-    k_bsucc_count<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
-    mark(ctx, s, "k_bsucc_scan");
-    k_bsucc_scan<<<count, 1024, 0, s>>>(d_inst, ctx->d_ws, count, A);
-    mark(ctx, s, "k_bsucc_fill");
-    k_bsucc_fill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    mark(ctx, s, "k_bsucc");
+    k_bsucc<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
     mark(ctx, s, "k_brec");
     k_brec<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
     // simulation: one warp per instance, launched per size class on forked

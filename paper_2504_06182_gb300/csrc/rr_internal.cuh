@@ -67,14 +67,13 @@ struct JobWS {
     int32_t nrecv, nev;
     // batching (Gamma + simulation)
     int64_t P;             // total path vertices (sum of path length + 1)
-    int64_t E;             // successor entries
     int32_t *pairOff;      // k + 1
     int32_t *cellCnt;      // m * n + 1 (counts, then exclusive offsets)
     int32_t *cellCur;      // m * n
     int32_t *cover;        // P
     int32_t *nextAt;       // P
-    int32_t *succOff;      // k + 1
-    int32_t *succ;         // E
+    int32_t *succCnt;      // k: distinct successors of each path
+    int32_t *succ;         // P: a path's successors at its vertex offset (pairOff)
     int32_t *indeg;        // k
     int4 *rec;             // k: packed geometry, successor count, overflow offset
     int4 *succ4;           // k: first four successors (flagged, -1 padded)
