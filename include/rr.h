@@ -188,6 +188,12 @@ int rr_plan_noalloc(const void *d_grid, int layout, int m, int n, rr_rect rect,
 int rr_set_tracing(rr_ctx *ctx, int enable);
 int rr_stage_times(rr_ctx *ctx, float *ms, const char **names, int cap);
 
+/* Kernels this context has launched since it was created (every public call
+ * adds the launches it made; the size-class simulation counts one launch per
+ * class). For accounting only: reading it does not synchronise. Returns
+ * RR_ERR_ARG for a null argument. */
+int rr_launch_count(rr_ctx *ctx, int64_t *launches);
+
 /* Last error text of this context (static storage, never NULL). */
 const char *rr_last_error(rr_ctx *ctx);
 

@@ -64,7 +64,7 @@ class rr_serve_result(ctypes.Structure):
 
 
 EXPORTS = ("rr_ctx_create", "rr_ctx_destroy", "rr_plan", "rr_batch", "rr_plan_batched", "rr_set_tracing",
-           "rr_stage_times", "rr_last_error", "rr_plan_noalloc", "rr_serve_open", "rr_serve_submit",
+           "rr_stage_times", "rr_launch_count", "rr_last_error", "rr_plan_noalloc", "rr_serve_open", "rr_serve_submit",
            "rr_serve_poll", "rr_serve_release", "rr_serve_close")
 RR_NOALLOC_MAX_SIDE = 256
 
@@ -94,6 +94,8 @@ def load(path: str = LIB_PATH):
     L.rr_set_tracing.restype = I32
     L.rr_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p), I32]
     L.rr_stage_times.restype = I32
+    L.rr_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    L.rr_launch_count.restype = I32
     L.rr_plan_noalloc.argtypes = [P, I32, I32, I32, rr_rect, P, I64, ctypes.POINTER(I64), P]
     L.rr_plan_noalloc.restype = I32
     L.rr_serve_open.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(rr_serve_config)]
@@ -187,6 +189,15 @@ def rr_stage_times(ctx, cap: int = 32):
     if k < 0:
         raise RRError(k, rr_last_error(ctx))
     return [(names[i].decode(), float(ms[i])) for i in range(k)]
+
+
+def rr_launch_count(ctx) -> int:
+    """Kernels the context has launched since it was created."""
+    v = ctypes.c_int64(0)
+    st = load().rr_launch_count(ctx, ctypes.byref(v))
+    if st != RR_OK:
+        raise RRError(st, rr_last_error(ctx))
+    return int(v.value)
 
 
 def rr_plan_noalloc(d_grid, layout, m, n, rect, d_moves, cap, stream=None):

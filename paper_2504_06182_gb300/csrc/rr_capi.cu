@@ -57,6 +57,7 @@ struct rr_ctx {
     int classListCap;
     cudaStream_t classStream[NCLASS];
     cudaEvent_t evFork, evJoin[NCLASS];
+    int64_t nlaunch;             // kernels launched so far
     // stage tracing: events recorded on the launching stream around every kernel
     int tracing;
     int nmarks;
@@ -198,6 +199,13 @@ extern "C" int rr_ctx_destroy(rr_ctx *ctx)
     return RR_OK;
 }
 
+extern "C" int rr_launch_count(rr_ctx *ctx, int64_t *launches)
+{
+    if (!ctx || !launches) return RR_ERR_ARG;
+    *launches = ctx->nlaunch;
+    return RR_OK;
+}
+
 extern "C" const char *rr_last_error(rr_ctx *ctx) { return ctx ? ctx->err : g_err; }
 
 static Arena arena_of(rr_ctx *ctx)
@@ -234,6 +242,7 @@ static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side
     k_emit_recv<<<dim3(recvBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
     mark(ctx, s, nullptr);
     CUDA_TRY(cudaGetLastError());
+    ctx->nlaunch += 6;
     return RR_OK;
 }
 
@@ -319,6 +328,7 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
     }
     mark(ctx, s, nullptr);
     CUDA_TRY(cudaGetLastError());
+    ctx->nlaunch += 15 + rr_ctx::NCLASS;
     return RR_OK;
 }
 
