@@ -368,6 +368,22 @@ def run_ours(args, rank, world, local):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         elapsed_ms = float(t.item())
 
+    # the same step replayed from a captured CUDA graph (RR_GRAPH)
+    gflags = rr.RR_WITH_BATCH | rr.RR_GRAPH
+    if rr.rr_plan_batched(P.ctx, d_inst, count, max_side, gflags, stream) != rr.RR_OK:
+        raise rr.RRError(-3, rr.rr_last_error(P.ctx))
+    torch.cuda.synchronize()
+    graph_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rr.rr_plan_batched(P.ctx, d_inst, count, max_side, gflags, stream)
+        b.record(stream)
+        b.synchronize()
+        graph_ms.append(a.elapsed_time(b))
+    graph_total = float(sum(graph_ms))
+
     res = unpack_instances(d_inst, count)
     tot_moves = sum(x.n_moves for x in res)
     tot_ops = sum(x.n_ops for x in res)
@@ -446,6 +462,8 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": count * world * args.steps / (e2e_total * 1e-3), "unit": "grids/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
+        "graph": {"value": count * args.steps / (graph_total * 1e-3), "unit": "grids/s",
+                  "note": "same step replayed from one captured CUDA graph (RR_GRAPH), inputs resident"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "plain": plain,

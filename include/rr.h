@@ -95,6 +95,7 @@ int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, int m, int n,
  * after synchronising the stream. */
 #define RR_WITH_BATCH 1
 #define RR_BATCH_ONLY 2   /* skip planning: instances carry moves and n_moves (status RR_OK) */
+#define RR_GRAPH 4        /* replay a captured CUDA graph of the launch sequence (below) */
 typedef struct {
     const void *grid;
     int32_t layout, m, n, pad0;
@@ -111,7 +112,16 @@ typedef struct {
  * count in [1, 65535]; max_side bounds m and n of every instance (an
  * instance above it gets RR_ERR_ARG); it sizes the launch shapes. The call
  * may grow the context's descriptor table (a synchronous cudaMalloc), so the
- * first call with a larger count must not be inside stream capture. */
+ * first call with a larger count must not be inside stream capture.
+ * With RR_GRAPH the context captures the call's whole launch sequence (one
+ * graph of all its kernels and memsets) the first time, on a stream of its
+ * own, and afterwards launches that graph on `stream` for as long as
+ * d_inst, count, max_side and flags stay the same; the descriptors and the
+ * memory they point to may change between calls (the kernels read them on
+ * the device). Any other call that grows the descriptor table drops the
+ * graph. Stage tracing does not cover graph launches. Nothing in the paper
+ * corresponds to this; it removes the per-call launch cost for callers that
+ * re-plan the same set of buffers (a control loop, the bench). */
 int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
                     cudaStream_t stream);
 

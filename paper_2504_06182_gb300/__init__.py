@@ -20,6 +20,7 @@ RR_ERR_TIMEOUT, RR_ERR_WORKSPACE, RR_ERR_INTERNAL = -4, -5, -6
 RR_U8, RR_BITS32 = 0, 1
 RR_WITH_BATCH = 1
 RR_BATCH_ONLY = 2
+RR_GRAPH = 4
 RR_MAX_SIDE = 1024
 STATUS_NAMES = {0: "OK", 1: "INFEASIBLE", -1: "ERR_ARG", -2: "ERR_CAPACITY", -3: "ERR_CUDA",
                 -4: "ERR_TIMEOUT", -5: "ERR_WORKSPACE", -6: "ERR_INTERNAL"}

@@ -888,7 +888,7 @@ __device__ void dissolve(const Sim<IX> &X, int nm, bool rowLine)
 
 // Instances grouped by size class (largest side <= classSide[c]) so that each
 // class's simulation launch gets shared memory sized for its own grids.
-__global__ void k_classify(rr_instance *inst, int count, int nclass, const int *classSide, int *classCount,
+__global__ void k_classify(rr_instance *inst, int count, int nclass, int max_side, int *classCount,
                            int *classList)
 {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
@@ -896,7 +896,7 @@ __global__ void k_classify(rr_instance *inst, int count, int nclass, const int *
         if (!live(I)) continue;
         const int side = max(I->m, I->n);
         int c = 0;
-        while (c < nclass - 1 && side > classSide[c]) ++c;
+        while (c < nclass - 1 && side > class_side(max_side, c, nclass)) ++c;
         classList[c * count + atomicAdd(&classCount[c], 1)] = q;
     }
 }

@@ -28,7 +28,7 @@ __global__ void k_bfill(rr_instance *, JobWS *, int);
 __global__ void k_bsort(rr_instance *, JobWS *, int);
 __global__ void k_bsucc(rr_instance *, JobWS *, int);
 __global__ void k_brec(rr_instance *, JobWS *, int);
-__global__ void k_classify(rr_instance *, int, int, const int *, int *, int *);
+__global__ void k_classify(rr_instance *, int, int, int, int *, int *);
 __global__ void k_sim16(rr_instance *, JobWS *, int, const int *, const int *, int, int);
 __global__ void k_sim32(rr_instance *, JobWS *, int, const int *, const int *, int, int);
 }  // namespace rrk
@@ -53,11 +53,18 @@ struct rr_ctx {
     // simulation size classes: side bounds, counts and lists (device), and a
     // stream per class forked from / joined into the caller's stream
     static const int NCLASS = 4;
-    int *d_classSide, *d_classCount, *d_classList;
+    int *d_classCount, *d_classList;
     int classListCap;
     cudaStream_t classStream[NCLASS];
     cudaEvent_t evFork, evJoin[NCLASS];
     int64_t nlaunch;             // kernels launched so far
+    // RR_GRAPH: the captured launch sequence and the call it belongs to
+    cudaStream_t capStream;
+    cudaGraphExec_t graph;
+    rr_instance *gInst;
+    int gCount, gMaxSide, gFlags;
+    int64_t gLaunches;
+    int capturing;
     // stage tracing: events recorded on the launching stream around every kernel
     int tracing;
     int nmarks;
@@ -67,7 +74,7 @@ struct rr_ctx {
 
 static void mark(rr_ctx *ctx, cudaStream_t s, const char *name)
 {
-    if (!ctx->tracing || ctx->nmarks >= 32) return;
+    if (!ctx->tracing || ctx->capturing || ctx->nmarks >= 32) return;
     if (!ctx->marks[ctx->nmarks]) cudaEventCreate(&ctx->marks[ctx->nmarks]);
     cudaEventRecord(ctx->marks[ctx->nmarks], s);
     ctx->names[ctx->nmarks] = name;
@@ -127,9 +134,17 @@ static int smem_limits(int dev, int *out)
     return RR_OK;
 }
 
+static void drop_graph(rr_ctx *ctx)
+{
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+    ctx->gInst = nullptr;
+}
+
 static int ensure_ws(rr_ctx *ctx, int count)
 {
     if (count <= ctx->ws_cap) return RR_OK;
+    drop_graph(ctx);          // it refers to the old table
     int cap = std::max(count, 2 * ctx->ws_cap);
     if (ctx->d_ws) CUDA_TRY(cudaFree(ctx->d_ws));
     ctx->d_ws = nullptr;
@@ -168,9 +183,9 @@ extern "C" int rr_ctx_create(rr_ctx **out, int64_t arena_bytes)
     if (st != RR_OK) { rr_ctx_destroy(ctx); return st; }
     st = ensure_ws(ctx, 1);
     if (st != RR_OK) { rr_ctx_destroy(ctx); return st; }
-    bool ok = cudaMalloc(&ctx->d_classSide, sizeof(int) * rr_ctx::NCLASS) == cudaSuccess &&
-              cudaMalloc(&ctx->d_classCount, sizeof(int) * rr_ctx::NCLASS) == cudaSuccess &&
-              cudaEventCreateWithFlags(&ctx->evFork, cudaEventDisableTiming) == cudaSuccess;
+    bool ok = cudaMalloc(&ctx->d_classCount, sizeof(int) * rr_ctx::NCLASS) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ctx->evFork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&ctx->capStream, cudaStreamNonBlocking) == cudaSuccess;
     for (int c = 0; ok && c < rr_ctx::NCLASS; ++c)
         ok = cudaStreamCreateWithFlags(&ctx->classStream[c], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&ctx->evJoin[c], cudaEventDisableTiming) == cudaSuccess;
@@ -186,7 +201,8 @@ extern "C" int rr_ctx_destroy(rr_ctx *ctx)
     cudaFree(ctx->d_top);
     cudaFree(ctx->d_one);
     cudaFree(ctx->d_ws);
-    cudaFree(ctx->d_classSide);
+    drop_graph(ctx);
+    if (ctx->capStream) cudaStreamDestroy(ctx->capStream);
     cudaFree(ctx->d_classCount);
     cudaFree(ctx->d_classList);
     if (ctx->evFork) cudaEventDestroy(ctx->evFork);
@@ -292,20 +308,16 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
     // streams so that each class's shared memory fits its own grids; slot
     // table, static lists and buffers live in shared memory (layout mirrored
     // in k_sim)
-    int sides[rr_ctx::NCLASS];
-    for (int c = 0; c < rr_ctx::NCLASS; ++c) sides[c] = std::max(32, (max_side * (c + 1) + rr_ctx::NCLASS - 1) / rr_ctx::NCLASS);
-    sides[rr_ctx::NCLASS - 1] = max_side;
-    CUDA_TRY(cudaMemcpyAsync(ctx->d_classSide, sides, sizeof(sides), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemsetAsync(ctx->d_classCount, 0, sizeof(int) * rr_ctx::NCLASS, s));
     mark(ctx, s, "k_classify");
-    k_classify<<<(count + 255) / 256, 256, 0, s>>>(d_inst, count, rr_ctx::NCLASS, ctx->d_classSide, ctx->d_classCount,
+    k_classify<<<(count + 255) / 256, 256, 0, s>>>(d_inst, count, rr_ctx::NCLASS, max_side, ctx->d_classCount,
                                                   ctx->d_classList);
     mark(ctx, s, "k_sim");
     CUDA_TRY(cudaEventRecord(ctx->evFork, s));
     for (int c = rr_ctx::NCLASS - 1; c >= 0; --c) {
         cudaStream_t cs = ctx->classStream[c];
         CUDA_TRY(cudaStreamWaitEvent(cs, ctx->evFork, 0));
-        const int side = sides[c];
+        const int side = class_side(max_side, c, rr_ctx::NCLASS);
         // ready moves never exceed two per column here (one chain head each
         // way); beyond the capacity slots spill to the global overflow area
         const int slotCap = 2 * side + 8, lineCap = side;
@@ -388,22 +400,63 @@ extern "C" int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, in
     return h.status;
 }
 
+// The whole sequence of one rr_plan_batched call on `stream`.
+static int launch_sequence(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
+                           cudaStream_t stream)
+{
+    CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
+    if (flags & RR_BATCH_ONLY) return launch_batch(ctx, d_inst, count, max_side, stream);
+    int st = launch_plan(ctx, d_inst, count, max_side, stream);
+    if (st != RR_OK) return st;
+    if (flags & RR_WITH_BATCH) st = launch_batch(ctx, d_inst, count, max_side, stream);
+    return st;
+}
+
 extern "C" int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
                                cudaStream_t stream)
 {
     if (!ctx || !d_inst || count < 1 || count > 65535 || max_side < 1 || max_side > RR_MAX_SIDE ||
-        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY)))
+        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY | RR_GRAPH)))
         return fail(ctx, RR_ERR_ARG, "rr_plan_batched: bad argument (count=%d max_side=%d flags=%d)", count,
                     max_side, flags);
     int st = ensure_ws(ctx, count);
     if (st != RR_OK) return st;
     ctx->nmarks = 0;
-    CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
-    if (flags & RR_BATCH_ONLY) return launch_batch(ctx, d_inst, count, max_side, stream);
-    st = launch_plan(ctx, d_inst, count, max_side, stream);
-    if (st != RR_OK) return st;
-    if (flags & RR_WITH_BATCH) st = launch_batch(ctx, d_inst, count, max_side, stream);
-    return st;
+    if (!(flags & RR_GRAPH)) return launch_sequence(ctx, d_inst, count, max_side, flags, stream);
+
+    if (!(ctx->graph && ctx->gInst == d_inst && ctx->gCount == count && ctx->gMaxSide == max_side &&
+          ctx->gFlags == flags)) {
+        // capture on the context's own stream (the caller's may be the legacy
+        // default stream, which cannot be captured); nothing runs yet
+        drop_graph(ctx);
+        const int64_t before = ctx->nlaunch;
+        CUDA_TRY(cudaStreamBeginCapture(ctx->capStream, cudaStreamCaptureModeThreadLocal));
+        ctx->capturing = 1;
+        st = launch_sequence(ctx, d_inst, count, max_side, flags, ctx->capStream);
+        ctx->capturing = 0;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ctx->capStream, &g);
+        if (st == RR_OK && e != cudaSuccess)
+            st = fail(ctx, RR_ERR_CUDA, "rr_plan_batched: graph capture: %s", cudaGetErrorString(e));
+        if (st == RR_OK) {
+            const cudaError_t e2 = cudaGraphInstantiate(&ctx->graph, g, 0);
+            if (e2 != cudaSuccess) {
+                ctx->graph = nullptr;
+                st = fail(ctx, RR_ERR_CUDA, "rr_plan_batched: graph instantiate: %s", cudaGetErrorString(e2));
+            }
+        }
+        if (g) cudaGraphDestroy(g);
+        ctx->gLaunches = ctx->nlaunch - before;
+        ctx->nlaunch = before;
+        if (st != RR_OK) {
+            cudaGetLastError();
+            return st;
+        }
+        ctx->gInst = d_inst; ctx->gCount = count; ctx->gMaxSide = max_side; ctx->gFlags = flags;
+    }
+    CUDA_TRY(cudaGraphLaunch(ctx->graph, stream));
+    ctx->nlaunch += ctx->gLaunches;
+    return RR_OK;
 }
 
 // Library-internal: size a context's descriptor table for `count` instances

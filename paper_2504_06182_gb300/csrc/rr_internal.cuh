@@ -87,6 +87,15 @@ struct JobWS {
     int32_t *ovfFree;      // k: recycled overflow slots
 };
 
+// Side bound of simulation size class c of nclass over grids up to
+// max_side (the last class takes max_side itself).
+__host__ __device__ inline int class_side(int max_side, int c, int nclass)
+{
+    if (c >= nclass - 1) return max_side;
+    const int s = (max_side * (c + 1) + nclass - 1) / nclass;
+    return s < 32 ? 32 : s;
+}
+
 // Shared memory of one batching-simulation block (one warp, one instance):
 // sort / merge buffer, slot table, id map, members, successor buffer,
 // pickup bitmaps, list links and heads (ix bytes each), step counters and

@@ -198,6 +198,56 @@ def test_batched_entry_point_mixed_sizes(planner):
         assert (mem[: r.n_members].cpu().numpy() == rmem).all()
 
 
+def test_batched_graph_replay(planner):
+    """RR_GRAPH: the first call captures the launch sequence, the second
+    replays it after new grids were written into the same buffers; both
+    results equal the oracle, and both calls count the same launches."""
+    import paper_2504_06182_gb300 as rr
+    from paper_2504_06182_gb300.planner import pack_instances, unpack_instances
+    sides = [32, 48, 96, 160, 256, 64, 200, 128]
+    sets = [[gridgen.square_instance(seed, g, s, 0.6) for g, s in enumerate(sides)] for seed in (31, 32)]
+    refs = [[oracle.plan(i.grid, i.rect) for i in insts] for insts in sets]
+
+    def steps_of(ref):
+        return int((np.abs(ref.moves[:, 0] - ref.moves[:, 2]) + np.abs(ref.moves[:, 1] - ref.moves[:, 3])).sum()) \
+            if len(ref.moves) else 0
+    entries, bufs = [], []
+    for g, s in enumerate(sides):
+        k = max(1, *(len(r[g].moves) for r in refs))
+        st = max(1, *(steps_of(r[g]) for r in refs))
+        grid = to_device(sets[0][g].grid, rr.RR_BITS32)
+        mv = torch.empty((k, 4), dtype=torch.int32, device="cuda")
+        ops = torch.empty((st, 3), dtype=torch.int32, device="cuda")
+        mem = torch.empty((st,), dtype=torch.int32, device="cuda")
+        entries.append(dict(grid=grid, layout=rr.RR_BITS32, m=s, n=s, rect=sets[0][g].rect, moves=mv, cap_moves=k,
+                            ops=ops, cap_ops=st, members=mem, cap_members=st))
+        bufs.append((grid, mv, ops, mem))
+    dev = pack_instances(entries)
+    flags = rr.RR_WITH_BATCH | rr.RR_GRAPH
+    counts = []
+    for which in (0, 1):
+        if which == 1:
+            for g, (grid, _, _, _) in enumerate(bufs):
+                grid.copy_(to_device(sets[1][g].grid, rr.RR_BITS32))
+        n0 = rr.rr_launch_count(planner.ctx)
+        assert rr.rr_plan_batched(planner.ctx, dev, len(sides), 256, flags) == rr.RR_OK
+        torch.cuda.synchronize()
+        counts.append(rr.rr_launch_count(planner.ctx) - n0)
+        res = unpack_instances(dev, len(sides))
+        for g, (r, ref) in enumerate(zip(res, refs[which])):
+            _, mv, ops, mem = bufs[g]
+            assert r.status == (rr.RR_OK if ref.status == 0 else rr.RR_INFEASIBLE), (which, g, r.status)
+            assert r.n_moves == len(ref.moves)
+            if ref.status != 0:
+                continue
+            assert (mv[: r.n_moves].cpu().numpy() == ref.moves).all()
+            rops, rmem = oracle.batch(ref.moves, sides[g], sides[g])
+            assert r.n_ops == len(rops) and r.n_members == len(rmem)
+            assert (ops[: r.n_ops].cpu().numpy() == rops).all()
+            assert (mem[: r.n_members].cpu().numpy() == rmem).all()
+    assert counts[0] == counts[1] > 0
+
+
 def test_grid_1024_bit_layout(planner):
     """Full-size 1024 x 1024 grid with a centred 720 x 720 target: the whole
     move list against the oracle, and the batches against the oracle (all of
