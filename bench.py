@@ -29,6 +29,11 @@ sys.path.insert(0, ROOT)
 
 import gridgen  # noqa: E402
 
+# The served run keeps dozens of streams busy; the device's default of 8
+# hardware work queues would make them wait on one another (set before CUDA
+# initialises; it lasts for this process only).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 METRIC = "red-rec grids/s and p50/p99 plan latency, batched/served vs plain; %HBM roof"
 WORKLOAD = "4096 square grids, side U{32..256 step 16}, p U[0.5,0.7], centred floor(0.7*side) target, bits32"
 
@@ -44,7 +49,8 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-sample", type=int, default=96, help="grids run one per call for the plain baseline")
-    ap.add_argument("--served-requests", type=int, default=2000, help="requests of the served run (0: skip)")
+    ap.add_argument("--served-requests", type=int, default=1000,
+                    help="requests of the served high-load run (0: skip the served runs)")
     ap.add_argument("--served-load", type=float, default=0.8, help="arrival rate as a fraction of saturation")
     return ap.parse_args()
 
@@ -190,17 +196,60 @@ def run_plain(rr, P, insts, sample):
 SERVED_SIDES = gridgen.SIDES_SERVED
 
 
-def run_served(rr, requests, load, seed=5):
-    """Continuous batching: Poisson arrivals of grids with side uniform in
-    {64, 80, ..., 512}, p = 0.6, centred floor(0.7 side) target, submitted from
-    host memory; latency = completion - submission per request."""
+def fifo_latencies(arrivals, service):
+    """Latency of each request when one server takes them in arrival order:
+    the plain path, one grid per call."""
+    free, out = 0.0, []
+    for ta, sv in zip(arrivals, service):
+        start = max(ta, free)
+        free = start + sv
+        out.append(free - ta)
+    return out
+
+
+def run_served(rr, requests, load, seed=5, slots=256, streams=32, max_wave=8, plain_n=48, lam_n=48):
+    """Served stream (C5): grids with side uniform in {64, 80, ..., 512},
+    p = 0.6, centred floor(0.7 side) target, submitted from host memory;
+    latency = completion - submission per request.
+
+    1. plain: the first plain_n pool grids one at a time (H2D of the grid,
+       rr_plan, rr_batch, synchronise): its maximum rate and service times;
+    2. Poisson arrivals at 0.5, 0.8 and 0.95 x that rate (lam_n requests
+       each, cycling through those grids): served p50/p99, and plain p50/p99
+       for the same arrivals from a first-in-first-out queue over the
+       measured service times;
+    3. saturation: a burst of the pool's requests at once;
+    4. Poisson arrivals at `load` x the served saturation (`requests`)."""
+    import torch
+    from paper_2504_06182_gb300.planner import Planner
     pool = []
-    for g in range(min(256, requests)):
+    for g in range(256):
         side, _ = gridgen.mixed_draw(seed, g, SERVED_SIDES, 0.6, 0.6)
         inst = gridgen.square_instance(seed, g, side, 0.6)
         pool.append((np.ascontiguousarray(gridgen.pack_bits32(inst.grid).view(np.int32)), inst))
-    srv = rr.rr_serve_open(max_side=512, slots=96, streams=4, max_wave=24, flags=rr.RR_WITH_BATCH,
-                           arena_bytes=6 << 30, heap_bytes=24 << 30)
+
+    # 1. plain, one grid per call
+    P = Planner(arena_bytes=2 << 30)
+    service = []
+    try:
+        for w, inst in pool[:1] + pool[:plain_n]:          # the first call warms up
+            s_ = inst.grid.shape[0]
+            t0 = time.perf_counter()
+            g = torch.from_numpy(w).cuda()
+            st, mv = P.plan(g, inst.rect, layout=rr.RR_BITS32, n=s_, cap=2 * s_ * s_)
+            if st == rr.RR_OK and len(mv):
+                P.batch(mv, s_, s_)
+            torch.cuda.synchronize()
+            service.append(time.perf_counter() - t0)
+    finally:
+        P.close()
+    service = service[1:]
+    plain_rate = len(service) / sum(service)
+
+    # workspace arenas: 48 GiB in total over the streams, at least 1 GiB each
+    arena = max(1 << 30, (48 << 30) // streams)
+    srv = rr.rr_serve_open(max_side=512, slots=slots, streams=streams, max_wave=max_wave, flags=rr.RR_WITH_BATCH,
+                           arena_bytes=arena, heap_bytes=24 << 30)
     try:
         def submit(i):
             w, inst = pool[i % len(pool)]
@@ -222,29 +271,52 @@ def run_served(rr, requests, load, seed=5):
                     keep.append(t)
             return keep
 
-        # saturation throughput: a burst of the pool's requests at once
+        def poisson(rate, n, index, rseed):
+            arrivals = np.cumsum(np.random.default_rng(rseed).exponential(1.0 / rate, size=n))
+            lat, outstanding = [], []
+            t0 = time.perf_counter()
+            for i, ta in enumerate(arrivals):
+                # drain finished requests, then sleep until the next arrival
+                # (the server's worker shares a mutex with polling: no spinning)
+                while True:
+                    outstanding = drain(outstanding, lat, False)
+                    wait = ta - (time.perf_counter() - t0)
+                    if wait <= 0:
+                        break
+                    time.sleep(min(wait, 0.002))
+                outstanding.append(submit(index(i)))
+            while outstanding:
+                outstanding = drain(outstanding, lat, True)
+            secs = time.perf_counter() - t0
+            return arrivals, np.array(lat) / 1e3, n / secs
+
+        # 2. arrivals at fractions of the plain rate
+        vs_plain = []
+        for k, frac in enumerate((0.5, 0.8, 0.95)):
+            rate = frac * plain_rate
+            arrivals, lat, _ = poisson(rate, lam_n, lambda i: i % plain_n, seed + 10 + k)
+            plat = np.array(fifo_latencies(arrivals, [service[i % plain_n] for i in range(lam_n)])) * 1e3
+            vs_plain.append({"rate_per_s": rate, "fraction_of_plain_max": frac, "requests": lam_n,
+                             "served_p50_ms": float(np.percentile(lat, 50)),
+                             "served_p99_ms": float(np.percentile(lat, 99)),
+                             "plain_p50_ms": float(np.percentile(plat, 50)),
+                             "plain_p99_ms": float(np.percentile(plat, 99))})
+        # 3. saturation throughput: a burst of the pool's requests at once
         nb = min(len(pool), 192)
         t0 = time.perf_counter()
         out = [submit(i) for i in range(nb)]
-        out = drain(out, [], True)
+        drain(out, [], True)
         sat = nb / (time.perf_counter() - t0)
-        # Poisson arrivals at `load` x saturation
-        rate = load * sat
-        rng = np.random.default_rng(seed)
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=requests))
-        lat, outstanding = [], []
-        t0 = time.perf_counter()
-        for i, ta in enumerate(arrivals):
-            while time.perf_counter() - t0 < ta:
-                outstanding = drain(outstanding, lat, False)
-            outstanding.append(submit(i))
-        while outstanding:
-            outstanding = drain(outstanding, lat, True)
-        secs = time.perf_counter() - t0
-        lat = np.array(lat) / 1e3
-        return {"requests": requests, "sides": "64..512 step 16", "p": 0.6, "rate_per_s": rate,
-                "saturation_grids_per_s": sat, "grids_per_s": requests / secs,
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        # 4. Poisson arrivals at `load` x saturation
+        _, lat, gps = poisson(load * sat, requests, lambda i: i, seed)
+        return {"sides": "64..512 step 16", "p": 0.6,
+                "server": {"slots": slots, "streams": streams, "max_wave": max_wave},
+                "plain_grids_per_s": plain_rate, "plain_sample": f"first {plain_n} pool grids, one call each",
+                "saturation_grids_per_s": sat,
+                "at_fraction_of_plain": vs_plain,
+                "high_load": {"rate_per_s": load * sat, "fraction_of_saturation": load, "requests": requests,
+                              "grids_per_s": gps, "p50_ms": float(np.percentile(lat, 50)),
+                              "p99_ms": float(np.percentile(lat, 99))},
                 "note": f"requests cycle through {len(pool)} distinct seeded grids"}
     finally:
         rr.rr_serve_close(srv)

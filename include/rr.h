@@ -134,7 +134,12 @@ int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, i
  * elementary steps is known, given result memory from a device heap and
  * batched in a second wave (memory-based admission). A worker thread owned
  * by the server drives the pipeline; the calling threads only submit, poll
- * and release. Results stay on the device until released. */
+ * and release. Results stay on the device until released. Each stream has a
+ * context of its own; a wave of at most 8 requests runs its simulation as
+ * one launch on its stream. With many streams, start the process with
+ * CUDA_DEVICE_MAX_CONNECTIONS=32 (read when CUDA initialises): with the
+ * default 8 hardware work queues, waves on different streams wait behind
+ * each other's long simulation kernels. */
 typedef struct rr_server rr_server;
 typedef struct {
     int32_t max_side;        /* largest m or n accepted, <= RR_MAX_SIDE */

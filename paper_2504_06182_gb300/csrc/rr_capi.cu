@@ -37,6 +37,9 @@ using namespace rrk;
 
 static_assert(sizeof(rr_instance) == 128, "rr_instance layout is part of the ABI");
 
+// Calls over at most this many grids run the simulation as one size class.
+static constexpr int SMALL_CALL = 8;
+
 // Kernels launched with more than the default 48 KB of dynamic shared memory.
 enum { SM_GSORT, SM_GSWEEP_H, SM_GSWEEP_V, SM_SIM16, SM_SIM32, SM_NKERNEL };
 
@@ -309,15 +312,20 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
     // table, static lists and buffers live in shared memory (layout mirrored
     // in k_sim)
     CUDA_TRY(cudaMemsetAsync(ctx->d_classCount, 0, sizeof(int) * rr_ctx::NCLASS, s));
+    // size classes, each launched on a stream of its own so that each gets
+    // shared memory for its own sides; a call over a few grids uses one
+    // class on the caller's stream (nothing to gain from the fork, and every
+    // extra stream shares the device's few hardware queues with the others)
+    const int nclass = count <= SMALL_CALL ? 1 : rr_ctx::NCLASS;
     mark(ctx, s, "k_classify");
-    k_classify<<<(count + 255) / 256, 256, 0, s>>>(d_inst, count, rr_ctx::NCLASS, max_side, ctx->d_classCount,
+    k_classify<<<(count + 255) / 256, 256, 0, s>>>(d_inst, count, nclass, max_side, ctx->d_classCount,
                                                   ctx->d_classList);
     mark(ctx, s, "k_sim");
-    CUDA_TRY(cudaEventRecord(ctx->evFork, s));
-    for (int c = rr_ctx::NCLASS - 1; c >= 0; --c) {
-        cudaStream_t cs = ctx->classStream[c];
-        CUDA_TRY(cudaStreamWaitEvent(cs, ctx->evFork, 0));
-        const int side = class_side(max_side, c, rr_ctx::NCLASS);
+    if (nclass > 1) CUDA_TRY(cudaEventRecord(ctx->evFork, s));
+    for (int c = nclass - 1; c >= 0; --c) {
+        cudaStream_t cs = nclass > 1 ? ctx->classStream[c] : s;
+        if (nclass > 1) CUDA_TRY(cudaStreamWaitEvent(cs, ctx->evFork, 0));
+        const int side = class_side(max_side, c, nclass);
         // ready moves never exceed two per column here (one chain head each
         // way); beyond the capacity slots spill to the global overflow area
         const int slotCap = 2 * side + 8, lineCap = side;
@@ -335,12 +343,14 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
             k_sim32<<<count, 32, simSmem, cs>>>(d_inst, ctx->d_ws, count, ctx->d_classList + (size_t)c * count,
                                                       ctx->d_classCount + c, slotCap, lineCap);
         }
-        CUDA_TRY(cudaEventRecord(ctx->evJoin[c], cs));
-        CUDA_TRY(cudaStreamWaitEvent(s, ctx->evJoin[c], 0));
+        if (nclass > 1) {
+            CUDA_TRY(cudaEventRecord(ctx->evJoin[c], cs));
+            CUDA_TRY(cudaStreamWaitEvent(s, ctx->evJoin[c], 0));
+        }
     }
     mark(ctx, s, nullptr);
     CUDA_TRY(cudaGetLastError());
-    ctx->nlaunch += 15 + rr_ctx::NCLASS;
+    ctx->nlaunch += 15 + nclass;
     return RR_OK;
 }
 
