@@ -167,6 +167,77 @@ def measured_traffic_ratio(kernel):
     return float(rec["ratio"])
 
 
+# ------------------------------------------------------------- paper geometry
+
+PAPER_NTX = (32, 64, 128, 256)
+PAPER_CONTEXT = {"n_tx": 32, "cpu_us": 106, "cpu_hw": "AMD Threadripper 2950X, serial",
+                 "gpu_us": 197, "gpu_hw": "Nvidia Quadro RTX 4000, one kernel"}
+
+
+def paper_instances():
+    """First feasible grid of seed 41 at each n_tx (n_tx columns,
+    ceil(n_tx / 0.6) rows, full-width target of n_tx rows)."""
+    out = []
+    for n_tx in PAPER_NTX:
+        for g in range(64):
+            inst = gridgen.paper_instance(41, g, n_tx)
+            # with a full-width target every column is a target column, so a
+            # grid is feasible iff its atoms cover the target cells
+            if int(inst.grid.sum()) >= n_tx * n_tx:
+                out.append(inst)
+                break
+    return out
+
+
+def median_us(fn, reps):
+    t = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        t.append(time.perf_counter() - t0)
+    return float(np.median(t) * 1e6)
+
+
+def oracle_paper_geometry():
+    """Single-thread oracle latency per grid at the paper's geometry."""
+    import oracle
+    oracle.build()
+    res = {}
+    for inst in paper_instances():
+        reps = 20 if inst.grid.shape[1] <= 64 else 3
+        plan_us = median_us(lambda: oracle.plan(inst.grid, inst.rect), reps)
+        p = oracle.plan(inst.grid, inst.rect)
+        both_us = median_us(lambda: oracle.batch(p.moves, *inst.grid.shape), reps) + plan_us
+        res[str(inst.grid.shape[1])] = {"plan_us": plan_us, "plan_batch_us": both_us}
+    return res
+
+
+def gpu_paper_geometry(rr, P):
+    """Plain GPU latency per grid at the paper's geometry: one rr_plan call
+    (grid resident on the device, counts back on the host), and rr_plan +
+    rr_batch."""
+    import torch
+    res = {}
+    for inst in paper_instances():
+        m, n = inst.grid.shape
+        g = torch.from_numpy(np.ascontiguousarray(gridgen.pack_bits32(inst.grid).view(np.int32))).cuda()
+        cap = 2 * m * n
+
+        def plan():
+            return P.plan(g, inst.rect, layout=rr.RR_BITS32, n=n, cap=cap)
+
+        def both():
+            st, mv = plan()
+            if st == rr.RR_OK and len(mv):
+                P.batch(mv, m, n)
+            torch.cuda.synchronize()
+        for _ in range(3):
+            both()
+        reps = 50 if n <= 64 else 10
+        res[str(n)] = {"plan_us": median_us(plan, reps), "plan_batch_us": median_us(both, reps)}
+    return res
+
+
 # ------------------------------------------------------------------ plain
 
 def run_plain(rr, P, insts, sample):
@@ -337,7 +408,8 @@ def run_ours(args, rank, world, local):
         done, secs = oracle_sample(insts, args.cpu_budget, threads)
         cpu = {"value": done / secs, "unit": "grids/s", "cores": threads, "kind": "oracle",
                "sample": f"first {done} grids of the workload (plan + batching), {threads} host threads, "
-                         f"{secs:.1f} s"}
+                         f"{secs:.1f} s",
+               "paper_geometry_1thread": oracle_paper_geometry()}
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -491,6 +563,9 @@ def run_ours(args, rank, world, local):
         return
 
     plain = run_plain(rr, P, insts, args.plain_sample) if args.plain_sample > 0 else None
+    paper = {"gpu": gpu_paper_geometry(rr, P), "paper_context": PAPER_CONTEXT,
+             "geometry": "n_tx columns, ceil(n_tx/0.6) rows, full-width target of n_tx rows, p = 0.6"} \
+        if args.plain_sample > 0 else None
     del ops, mem, moves
     P.close()
     torch.cuda.empty_cache()
@@ -539,6 +614,7 @@ def run_ours(args, rank, world, local):
         "roofline": roof,
         "cpu_baseline": cpu,
         "plain": plain,
+        "paper_geometry": paper,
         "served": served,
         "clocks": clk,
         "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_tot.items(), key=lambda kv: -kv[1])},

@@ -106,6 +106,15 @@ def square_instance(seed: int, g: int, side: int, p: float, target: int | None =
     return Instance(grid, centred_rect(side, side, t, t), seed, g, p)
 
 
+def paper_instance(seed: int, g: int, n_tx: int, p: float = 0.6) -> Instance:
+    """The paper's runtime geometry: n_tx columns and ceil(n_tx / 0.6) rows
+    (integer form: (5 n_tx + 2) // 3), fill p, a full-width target of n_tx
+    rows centred vertically."""
+    m = (5 * n_tx + 2) // 3
+    grid = grid_u8(seed, g, m, n_tx, threshold(p))
+    return Instance(grid, centred_rect(m, n_tx, n_tx, n_tx), seed, g, p)
+
+
 def mixed_draw(seed: int, g: int, sides, p_lo: float, p_hi: float):
     """Per-grid (side, p) for mixed-size workloads: side uniform over `sides`,
     p uniform in [p_lo, p_hi], both from outputs 2**32 and 2**32 + 1 of grid

@@ -100,6 +100,29 @@ def test_grid_256_byte_layout(planner, seed):
     assert ref.status == 0
 
 
+@pytest.mark.parametrize("n_tx", [32, 48, 64, 100, 128])
+def test_paper_geometry(planner, n_tx):
+    """The paper's runtime geometry (n_tx columns, ceil(n_tx / 0.6) rows,
+    full-width target of n_tx rows): plans and batches equal the oracle in
+    both grid layouts."""
+    from paper_2504_06182_gb300 import RR_BITS32, RR_U8
+    # at this geometry about as many atoms as targets are expected: take the
+    # first feasible and the first infeasible instance of the seed
+    seen = set()
+    for g in range(40):
+        inst = gridgen.paper_instance(41, g, n_tx)
+        assert inst.rect[1] == 0 and inst.rect[3] == n_tx
+        ref = oracle.plan(inst.grid, inst.rect)
+        if ref.status in seen:
+            continue
+        seen.add(ref.status)
+        check_instance(planner, inst.grid, inst.rect, RR_U8)
+        check_instance(planner, inst.grid, inst.rect, RR_BITS32, with_batch=False)
+        if len(seen) == 2:
+            break
+    assert seen == {0, 1}
+
+
 def test_edge_cases(planner):
     from paper_2504_06182_gb300 import RR_BITS32, RR_U8
     cases = []
