@@ -127,8 +127,9 @@ int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, i
 
 /* ------------------------------------------------------------------ serving
  * Continuous batching of planning requests (red-rec + batching per request):
- * requests are admitted into preallocated device slots as they arrive and
- * as slots free up, planned in waves (one rr_plan_batched call over the
+ * a request is admitted as soon as its grid and its move list (room for
+ * 2 m n moves, each atom moves at most twice) fit in the device input pool
+ * and fewer than `slots` requests are resident (first come, first served), planned in waves (one rr_plan_batched call over the
  * requests admitted since the previous wave) on a pool of streams so that
  * waves overlap on the device, and, once a request's exact number of
  * elementary steps is known, given result memory from a device heap and
@@ -143,13 +144,15 @@ int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, i
 typedef struct rr_server rr_server;
 typedef struct {
     int32_t max_side;        /* largest m or n accepted, <= RR_MAX_SIDE */
-    int32_t slots;           /* requests resident at once (device grid + move buffers) */
+    int32_t slots;           /* requests admitted and not yet released, at most */
     int32_t streams;         /* waves in flight at once */
     int32_t max_wave;        /* requests per wave, <= slots */
     int32_t flags;           /* RR_WITH_BATCH to also batch every plan */
     int32_t pad;
     int64_t arena_bytes;     /* workspace arena per stream */
     int64_t heap_bytes;      /* device heap for batch results (16 B per elementary step) */
+    int64_t input_bytes;     /* device pool for grids and move lists; 0: room for `slots`
+                                requests of max_side */
 } rr_serve_config;
 typedef struct {
     int32_t status;          /* RR_OK, RR_INFEASIBLE or an error; RR_ERR_CAPACITY if the heap can never hold it */
@@ -163,7 +166,9 @@ typedef struct {
 /* Allocates every device buffer up front (slots, heap, arenas, descriptors). */
 int rr_serve_open(rr_server **srv, const rr_serve_config *cfg);
 /* Copies the grid (host memory, layouts as rr_plan) into the request queue
- * and returns a ticket at once. RR_ERR_ARG for sizes above max_side. */
+ * and returns a ticket at once. RR_ERR_ARG for sizes above max_side;
+ * RR_ERR_CAPACITY if the grid and its move list could never fit the input
+ * pool. */
 int rr_serve_submit(rr_server *srv, const void *h_grid, int layout, int m, int n, rr_rect rect,
                     int64_t *ticket);
 /* Waits up to timeout_us (0: just look) for the ticket: RR_OK and *out

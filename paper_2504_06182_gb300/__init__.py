@@ -53,7 +53,7 @@ class rr_instance(ctypes.Structure):
 class rr_serve_config(ctypes.Structure):
     _fields_ = [("max_side", ctypes.c_int32), ("slots", ctypes.c_int32), ("streams", ctypes.c_int32),
                 ("max_wave", ctypes.c_int32), ("flags", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("arena_bytes", ctypes.c_int64), ("heap_bytes", ctypes.c_int64)]
+                ("arena_bytes", ctypes.c_int64), ("heap_bytes", ctypes.c_int64), ("input_bytes", ctypes.c_int64)]
 
 
 class rr_serve_result(ctypes.Structure):
@@ -212,9 +212,10 @@ def rr_plan_noalloc(d_grid, layout, m, n, rect, d_moves, cap, stream=None):
 
 # ------------------------------------------------------------------ serving
 
-def rr_serve_open(max_side, slots, streams, max_wave, flags=RR_WITH_BATCH, arena_bytes=0, heap_bytes=1 << 30):
+def rr_serve_open(max_side, slots, streams, max_wave, flags=RR_WITH_BATCH, arena_bytes=0, heap_bytes=1 << 30,
+                  input_bytes=0):
     cfg = rr_serve_config(int(max_side), int(slots), int(streams), int(max_wave), int(flags), 0,
-                          int(arena_bytes), int(heap_bytes))
+                          int(arena_bytes), int(heap_bytes), int(input_bytes))
     h = ctypes.c_void_p(0)
     st = load().rr_serve_open(ctypes.byref(h), ctypes.byref(cfg))
     if st != RR_OK:

@@ -1,6 +1,7 @@
 // rr_serve.cu -- continuous batching of planning requests (include/rr.h,
-// "serving"). A worker thread admits queued requests into preallocated
-// device slots, plans them in waves with rr_plan_batched on a pool of
+// "serving"). A worker thread admits queued requests as their grid and move
+// buffers fit in a device input pool, plans them in waves with
+// rr_plan_batched on a pool of
 // streams (one context, hence one workspace arena, per stream, so waves run
 // concurrently on the device), gives each planned request result memory from
 // a device heap once its exact size (16 B per elementary step) is known, and
@@ -29,7 +30,7 @@ struct Req {
     std::vector<uint8_t> grid;
     int layout = 0, m = 0, n = 0;
     rr_rect rect{0, 0, 0, 0};
-    int slot = -1;
+    int64_t inOff = -1, inBytes = 0;          // grid + move list in the input pool
     int64_t heapOff = -1, heapBytes = 0;
     int phase = QUEUED;
     rr_instance desc{};
@@ -75,15 +76,20 @@ struct Heap {
     }
 };
 
+// Room for a request's moves: every atom moves at most twice (an outer
+// column's atom once in its column, once to a receiver), and there are at
+// most m n atoms.
+int64_t moves_cap(int m, int n) { return 2ll * m * n; }
+
 }  // namespace
 
 struct rr_server {
     rr_serve_config cfg{};
     int device = 0;
-    int64_t gridBytes = 0, movesCap = 0;
-    std::vector<void *> slotGrid;
-    std::vector<rr_move *> slotMoves;
-    std::vector<int> freeSlots;
+    int64_t gridBytes = 0;                    // largest grid (staging buffers)
+    char *inBase = nullptr;                   // input pool: grids and move lists
+    Heap inHeap;
+    int resident = 0;                         // admitted, not yet released
     std::vector<rr_ctx *> ctx;
     std::vector<cudaStream_t> stream;
     std::vector<Wave> wave;
@@ -190,32 +196,39 @@ static bool pump(rr_server *S)
         W.busy = true; W.kind = 2;
         did = true;
     }
-    // 3. plan waves for queued requests, as device slots free up
-    for (int s = 0; s < NS && !S->queued.empty() && !S->freeSlots.empty(); ++s) {
+    // 3. plan waves for queued requests, admitted first come first served as
+    // their grid and move list fit in the input pool
+    for (int s = 0; s < NS && !S->queued.empty() && S->resident < S->cfg.slots; ++s) {
         Wave &W = S->wave[s];
         if (W.busy) continue;
         cudaStream_t st = S->stream[s];
         int cnt = 0, e = cudaSuccess;
-        while (!S->queued.empty() && !S->freeSlots.empty() && cnt < S->cfg.max_wave) {
+        while (!S->queued.empty() && S->resident < S->cfg.slots && cnt < S->cfg.max_wave) {
             Req *R = S->queued.front();
+            const int64_t gb = Heap::round((int64_t)R->grid.size());
+            const int64_t cap = moves_cap(R->m, R->n);
+            const int64_t bytes = gb + Heap::round(cap * (int64_t)sizeof(rr_move));
+            const int64_t off = S->inHeap.alloc(bytes);
+            if (off < 0) break;                                  // wait for releases
             S->queued.pop_front();
-            R->slot = S->freeSlots.back();
-            S->freeSlots.pop_back();
+            R->inOff = off; R->inBytes = bytes;
+            ++S->resident;
             R->tAdmit = S->now();
             uint8_t *stage = S->hStage[s] + (size_t)cnt * S->gridBytes;
             std::memcpy(stage, R->grid.data(), R->grid.size());
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(S->slotGrid[R->slot], stage, R->grid.size(), cudaMemcpyHostToDevice, st);
+                e = cudaMemcpyAsync(S->inBase + off, stage, R->grid.size(), cudaMemcpyHostToDevice, st);
             rr_instance d{};
-            d.grid = S->slotGrid[R->slot];
+            d.grid = S->inBase + off;
             d.layout = R->layout; d.m = R->m; d.n = R->n; d.rect = R->rect;
-            d.moves = S->slotMoves[R->slot];
-            d.cap_moves = S->movesCap;
+            d.moves = (rr_move *)(S->inBase + off + gb);
+            d.cap_moves = cap;
             S->hDesc[s][cnt] = d;
             R->phase = PLANNING;
             W.reqs.push_back(R);
             ++cnt;
         }
+        if (!cnt) break;                                         // the head of the queue does not fit yet
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(S->dDesc[s], S->hDesc[s], sizeof(rr_instance) * cnt, cudaMemcpyHostToDevice, st);
         int r = e == cudaSuccess ? rr_plan_batched(S->ctx[s], S->dDesc[s], cnt, S->cfg.max_side, 0, st) : RR_ERR_CUDA;
@@ -253,8 +266,7 @@ static void destroy(rr_server *S)
     for (auto *p : S->hDesc) if (p) cudaFreeHost(p);
     for (auto *p : S->dDesc) if (p) cudaFree(p);
     for (auto *p : S->hStage) if (p) cudaFreeHost(p);
-    for (auto *p : S->slotGrid) if (p) cudaFree(p);
-    for (auto *p : S->slotMoves) if (p) cudaFree(p);
+    if (S->inBase) cudaFree(S->inBase);
     if (S->heapBase) cudaFree(S->heapBase);
     for (auto &kv : S->reqs) delete kv.second;
     delete S;
@@ -264,7 +276,7 @@ extern "C" int rr_serve_open(rr_server **out, const rr_serve_config *cfg)
 {
     if (!out || !cfg || cfg->max_side < 1 || cfg->max_side > RR_MAX_SIDE || cfg->slots < 1 || cfg->streams < 1 ||
         cfg->streams > 64 || cfg->max_wave < 1 || cfg->max_wave > cfg->slots || cfg->max_wave > 65535 ||
-        (cfg->flags & ~RR_WITH_BATCH) || cfg->heap_bytes < 0)
+        (cfg->flags & ~RR_WITH_BATCH) || cfg->heap_bytes < 0 || cfg->input_bytes < 0)
         return RR_ERR_ARG;
     *out = nullptr;
     rr_server *S = new (std::nothrow) rr_server();
@@ -273,15 +285,12 @@ extern "C" int rr_serve_open(rr_server **out, const rr_serve_config *cfg)
     S->t0 = Clock::now();
     const int ms = cfg->max_side;
     S->gridBytes = std::max<int64_t>((int64_t)ms * ms, (int64_t)ms * ((ms + 31) / 32) * 4);
-    S->movesCap = 2ll * ms * ms;
     bool ok = cudaGetDevice(&S->device) == cudaSuccess;
-    for (int i = 0; ok && i < cfg->slots; ++i) {
-        void *g = nullptr, *mv = nullptr;
-        ok = cudaMalloc(&g, S->gridBytes) == cudaSuccess && cudaMalloc(&mv, sizeof(rr_move) * S->movesCap) == cudaSuccess;
-        S->slotGrid.push_back(g);
-        S->slotMoves.push_back((rr_move *)mv);
-        S->freeSlots.push_back(cfg->slots - 1 - i);
-    }
+    // input pool: by default room for `slots` requests of the largest size
+    const int64_t one = Heap::round(S->gridBytes) + Heap::round(moves_cap(ms, ms) * (int64_t)sizeof(rr_move));
+    const int64_t pool = cfg->input_bytes > 0 ? cfg->input_bytes : one * cfg->slots;
+    ok = ok && cudaMalloc(&S->inBase, pool) == cudaSuccess;
+    S->inHeap.init(ok ? pool : 0);
     if (ok && cfg->heap_bytes > 0) ok = cudaMalloc(&S->heapBase, cfg->heap_bytes) == cudaSuccess;
     S->heap.init(ok ? cfg->heap_bytes : 0);
     S->ctx.assign(cfg->streams, nullptr);
@@ -314,6 +323,10 @@ extern "C" int rr_serve_submit(rr_server *S, const void *h_grid, int layout, int
     Req *R = new (std::nothrow) Req();
     if (!R) return RR_ERR_ARG;
     const size_t bytes = layout == RR_U8 ? (size_t)m * n : (size_t)m * ((n + 31) / 32) * 4;
+    if (Heap::round((int64_t)bytes) + Heap::round(moves_cap(m, n) * (int64_t)sizeof(rr_move)) > S->inHeap.size) {
+        delete R;
+        return RR_ERR_CAPACITY;                  // could never be admitted
+    }
     R->grid.assign((const uint8_t *)h_grid, (const uint8_t *)h_grid + bytes);
     R->layout = layout; R->m = m; R->n = n; R->rect = rect;
     std::lock_guard<std::mutex> lk(S->mu);
@@ -343,7 +356,8 @@ extern "C" int rr_serve_poll(rr_server *S, int64_t ticket, rr_serve_result *out,
     out->m = R->m; out->n = R->n;
     out->n_moves = R->desc.n_moves; out->n_steps = R->desc.n_steps;
     out->n_ops = R->desc.n_ops; out->n_members = R->desc.n_members;
-    out->d_moves = R->slot >= 0 ? S->slotMoves[R->slot] : nullptr;
+    out->d_moves = R->inOff >= 0 ? (const rr_move *)(S->inBase + R->inOff + Heap::round((int64_t)R->grid.size()))
+                                 : nullptr;
     out->d_ops = R->heapOff >= 0 ? (const rr_op *)(S->heapBase + R->heapOff) : nullptr;
     out->d_members = R->heapOff >= 0 ? (const int32_t *)(S->heapBase + R->heapOff + 12 * R->desc.n_steps) : nullptr;
     out->t_submit_us = R->tSubmit; out->t_admit_us = R->tAdmit; out->t_done_us = R->tDone;
@@ -357,7 +371,7 @@ extern "C" int rr_serve_release(rr_server *S, int64_t ticket)
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end() || it->second->phase != DONE) return RR_ERR_ARG;
     Req *R = it->second;
-    if (R->slot >= 0) S->freeSlots.push_back(R->slot);
+    if (R->inOff >= 0) { S->inHeap.release(R->inOff, R->inBytes); --S->resident; }
     if (R->heapOff >= 0) S->heap.release(R->heapOff, R->heapBytes);
     S->reqs.erase(it);
     delete R;

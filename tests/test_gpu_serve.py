@@ -59,3 +59,43 @@ def test_served_results_equal_alone():
     finally:
         rr.rr_serve_close(srv)
         P.close()
+
+
+def test_served_admission_by_memory():
+    """A small input pool (room for about three 256 x 256 requests) admits
+    requests as their grid and move list fit: every result still equals
+    the request planned alone, and a grid that could never fit is refused."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2504_06182_gb300 as rr
+    from paper_2504_06182_gb300.planner import Planner, device_view
+
+    insts = gridgen.mixed_instances(78, 24, sides=(32, 64, 128, 256), p_lo=0.6, p_hi=0.65)
+    per_max = 256 * 256 + 2 * 256 * 256 * 16           # grid bytes + move list of a 256 x 256 request
+    srv = rr.rr_serve_open(max_side=512, slots=24, streams=4, max_wave=4, flags=rr.RR_WITH_BATCH,
+                           arena_bytes=1 << 30, heap_bytes=1 << 30, input_bytes=3 * per_max + (1 << 20))
+    P = Planner(arena_bytes=1 << 30)
+    try:
+        big = np.zeros((512, 512), np.uint8)
+        assert rr.rr_serve_submit(srv, big, rr.RR_U8, 512, 512, (1, 1, 511, 511))[0] == rr.RR_ERR_CAPACITY
+        tickets = []
+        for inst in insts:
+            m, n = inst.grid.shape
+            st, t = rr.rr_serve_submit(srv, np.ascontiguousarray(inst.grid), rr.RR_U8, m, n, inst.rect)
+            assert st == rr.RR_OK
+            tickets.append(t)
+        for inst, t in zip(insts, tickets):
+            st, res = rr.rr_serve_poll(srv, t, timeout_us=120_000_000)
+            assert st == rr.RR_OK, st
+            m, n = inst.grid.shape
+            st_ref, mv_ref = P.plan(torch.from_numpy(inst.grid).cuda(), inst.rect, layout=rr.RR_U8, n=n)
+            assert res.status == st_ref and res.n_moves == len(mv_ref)
+            assert torch.equal(device_view(res.d_moves, (res.n_moves, 4)), mv_ref)
+            if st_ref == rr.RR_OK and len(mv_ref):
+                ops_ref, mem_ref = P.batch(mv_ref, m, n)
+                assert torch.equal(device_view(res.d_ops, (res.n_ops, 3)), ops_ref)
+                assert torch.equal(device_view(res.d_members, (res.n_members,)), mem_ref)
+            assert rr.rr_serve_release(srv, t) == rr.RR_OK
+    finally:
+        rr.rr_serve_close(srv)
+        P.close()
