@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=1000,
                     help="requests of the served high-load run (0: skip the served runs)")
     ap.add_argument("--served-load", type=float, default=0.8, help="arrival rate as a fraction of saturation")
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the bench line: one line per single-grid config (32^2, 256^2, 1024^2), "
+                         "plain GPU latency and the single-thread oracle, median over seeds")
     return ap.parse_args()
 
 
@@ -657,9 +660,95 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------- single-grid configs
+
+SINGLE_CONFIGS = (
+    ("32x32 u8, p = 0.6, centred 20x20 target", 32, 20, "u8"),
+    ("256x256 u8, p = 0.6, centred 180x180 target", 256, 180, "u8"),
+    ("1024x1024 bits32, p = 0.6, centred 720x720 target", 1024, 720, "bits32"),
+)
+
+
+def path_steps(moves):
+    return int((np.abs(moves[:, 0] - moves[:, 2]) + np.abs(moves[:, 1] - moves[:, 3])).sum()) if len(moves) else 0
+
+
+def run_configs(args):
+    """Plain per-grid latency of each single-grid config on seeds 0..9 (GPU:
+    one rr_plan call, and rr_plan + rr_batch, grid resident on the device)
+    and, as this mode's CPU baseline, the single-thread oracle on the same
+    grids (1024^2: planning on seeds 0..2 and the first 200 000 batches of
+    seed 0, a bounded sample). Medians over seeds."""
+    import oracle
+    oracle.build()
+    seeds = list(range(10))
+    cpu = {}
+    for name, side, t, _ in SINGLE_CONFIGS:
+        plan_us, both_us, sample = [], [], ""
+        for sd in (seeds if side < 1024 else seeds[:3]):
+            inst = gridgen.square_instance(sd, 0, side, 0.6, t)
+            t0 = time.perf_counter()
+            p = oracle.plan(inst.grid, inst.rect)
+            t1 = time.perf_counter()
+            plan_us.append((t1 - t0) * 1e6)
+            if side < 1024:
+                oracle.batch(p.moves, side, side, cap=path_steps(p.moves))
+                both_us.append((time.perf_counter() - t0) * 1e6)
+            elif sd == 0:
+                t2 = time.perf_counter()
+                ops, _ = oracle.batch(p.moves, side, side, max_ops=200000, cap=path_steps(p.moves))
+                rate = len(ops) / (time.perf_counter() - t2)
+                sample = f"planning on seeds 0..2; batching: the first {len(ops)} batches of seed 0 " \
+                         f"at {rate:.0f} batches/s"
+        cpu[side] = {"kind": "oracle", "cores": 1, "plan_us": float(np.median(plan_us)),
+                     "plan_batch_us": float(np.median(both_us)) if both_us else None,
+                     "sample": sample or f"seeds 0..{seeds[-1]}, one grid at a time"}
+    import torch
+    import paper_2504_06182_gb300 as rr
+    from paper_2504_06182_gb300.planner import Planner
+    P = Planner(arena_bytes=4 << 30)
+    for name, side, t, lay in SINGLE_CONFIGS:
+        layout = rr.RR_U8 if lay == "u8" else rr.RR_BITS32
+        plan_us, both_us, outs = [], [], None
+        for sd in seeds:
+            inst = gridgen.square_instance(sd, 0, side, 0.6, t)
+            host = inst.grid if lay == "u8" else gridgen.pack_bits32(inst.grid).view(np.int32)
+            g = torch.from_numpy(np.ascontiguousarray(host)).cuda()
+            cap = 2 * side * side
+
+            def plan():
+                r = P.plan(g, inst.rect, layout=layout, n=side, cap=cap)
+                torch.cuda.synchronize()
+                return r
+
+            def both():
+                st, mv = plan()
+                res = P.batch(mv, side, side) if st == rr.RR_OK and len(mv) else None
+                torch.cuda.synchronize()
+                return st, mv, res
+            both()
+            reps = 20 if side <= 256 else 2
+            plan_us.append(median_us(plan, reps))
+            both_us.append(median_us(both, max(2, reps // 4)))
+            if sd == 0:
+                st, mv, res = both()
+                outs = {"status": int(st), "moves": int(len(mv)),
+                        "ops": int(len(res[0])) if res else 0, "steps": int(len(res[1])) if res else 0}
+        line = {"config": name, "metric": "plain per-grid latency (median over seeds 0..9)", "unit": "us",
+                "gpu": {"plan_us": float(np.median(plan_us)), "plan_batch_us": float(np.median(both_us)),
+                        "path": "one rr_plan (and rr_batch) call per grid, grid resident on the device, synchronised"},
+                "cpu_baseline": cpu[side], "seed0_outputs": outs, "data": "synthetic"}
+        print(json.dumps(line), flush=True)
+    P.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.configs:
+        if rank == 0:
+            run_configs(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -106,13 +106,15 @@ def plan(grid: np.ndarray, rect, with_trace: bool = False) -> Plan:
                 events[: ne.value].copy() if with_trace else None)
 
 
-def batch(moves: np.ndarray, m: int, n: int, max_ops: int | None = None):
+def batch(moves: np.ndarray, m: int, n: int, max_ops: int | None = None, cap: int = 0):
     """Returns (ops (b, 3) int32: dir, first, count; members (s,) int32).
-    With max_ops, only the first max_ops batches."""
+    With max_ops, only the first max_ops batches. cap: initial room for ops
+    and members (a caller that knows the total path length passes it and
+    the routine runs once instead of sizing first)."""
     moves = np.ascontiguousarray(moves, dtype=np.int32).reshape(-1, 4)
     no = ctypes.c_int64(0)
     nmem = ctypes.c_int64(0)
-    cap_o = cap_m = 0
+    cap_o = cap_m = int(cap)
     while True:
         ops = np.zeros((max(cap_o, 1), 3), dtype=np.int32)
         mem = np.zeros(max(cap_m, 1), dtype=np.int32)
