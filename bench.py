@@ -475,6 +475,9 @@ def run_ours(args, rank, world, local):
         if st != rr.RR_OK:
             raise rr.RRError(st, rr.rr_last_error(P.ctx))
 
+    # launch configuration picked by the library's autotuner on this workload
+    # (before the warm-up; not timed)
+    tuned_nclass, tuned_shift = rr.rr_autotune(P.ctx, d_inst, count, max_side, rr.RR_WITH_BATCH, stream)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -608,7 +611,8 @@ def run_ours(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grids_per_gpu": count, "layout": "bits32", "seed": args.seed,
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world}"},
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world}",
+                   "autotuned": {"size_classes": tuned_nclass, "block_budget_scale": 2.0 ** tuned_shift}},
         "e2e": {"value": count * world * args.steps / (e2e_total * 1e-3), "unit": "grids/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,

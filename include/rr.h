@@ -125,6 +125,19 @@ typedef struct {
 int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
                     cudaStream_t stream);
 
+/* Launch-configuration autotuner for rr_plan_batched (nothing in the paper
+ * corresponds to it). Runs the call's launch sequence on these instances
+ * under nine configurations: 2, 4 or 8 simulation size classes, times per-grid
+ * block budgets of the planning and graph kernels scaled by 1/2, 1 or 2. Each
+ * is timed with CUDA events on `stream`, best of two. The fastest is kept in
+ * the context for later rr_plan_batched calls (any captured RR_GRAPH graph is
+ * dropped), and written to *nclass and *shift (log2 of the budget scale) when
+ * those are not NULL. Every configuration computes the same results, so the
+ * descriptors and outputs hold this call's results afterwards. Synchronises;
+ * flags as rr_plan_batched without RR_GRAPH. */
+int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
+                cudaStream_t stream, int32_t *nclass, int32_t *shift);
+
 /* ------------------------------------------------------------------ serving
  * Continuous batching of planning requests (red-rec + batching per request):
  * a request is admitted as soon as its grid and its move list (room for

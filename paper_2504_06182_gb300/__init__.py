@@ -65,7 +65,7 @@ class rr_serve_result(ctypes.Structure):
 
 
 EXPORTS = ("rr_ctx_create", "rr_ctx_destroy", "rr_plan", "rr_batch", "rr_plan_batched", "rr_set_tracing",
-           "rr_stage_times", "rr_launch_count", "rr_last_error", "rr_plan_noalloc", "rr_serve_open", "rr_serve_submit",
+           "rr_stage_times", "rr_launch_count", "rr_autotune", "rr_last_error", "rr_plan_noalloc", "rr_serve_open", "rr_serve_submit",
            "rr_serve_poll", "rr_serve_release", "rr_serve_close")
 RR_NOALLOC_MAX_SIDE = 256
 
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
     L.rr_stage_times.restype = I32
     L.rr_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     L.rr_launch_count.restype = I32
+    L.rr_autotune.argtypes = [P, P, I32, I32, I32, P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.rr_autotune.restype = I32
     L.rr_plan_noalloc.argtypes = [P, I32, I32, I32, rr_rect, P, I64, ctypes.POINTER(I64), P]
     L.rr_plan_noalloc.restype = I32
     L.rr_serve_open.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(rr_serve_config)]
@@ -190,6 +192,17 @@ def rr_stage_times(ctx, cap: int = 32):
     if k < 0:
         raise RRError(k, rr_last_error(ctx))
     return [(names[i].decode(), float(ms[i])) for i in range(k)]
+
+
+def rr_autotune(ctx, d_inst, count, max_side, flags=RR_WITH_BATCH, stream=None):
+    """Picks and keeps the fastest launch configuration for these instances.
+    Returns (size classes, log2 block-budget scale)."""
+    nc, sh = ctypes.c_int32(0), ctypes.c_int32(0)
+    st = load().rr_autotune(ctx, _addr(d_inst), int(count), int(max_side), int(flags), _stream(stream),
+                            ctypes.byref(nc), ctypes.byref(sh))
+    if st != RR_OK:
+        raise RRError(st, rr_last_error(ctx))
+    return int(nc.value), int(sh.value)
 
 
 def rr_launch_count(ctx) -> int:

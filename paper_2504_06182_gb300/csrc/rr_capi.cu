@@ -55,11 +55,14 @@ struct rr_ctx {
     char err[256];
     // simulation size classes: side bounds, counts and lists (device), and a
     // stream per class forked from / joined into the caller's stream
-    static const int NCLASS = 4;
+    static const int MAXCLASS = 8;
+    // launch configuration of batched calls (rr_autotune may change it):
+    // simulation size classes, and per-grid block budgets scaled by 2^shift
+    int nclass = 4, shift = 0;
     int *d_classCount, *d_classList;
     int classListCap;
-    cudaStream_t classStream[NCLASS];
-    cudaEvent_t evFork, evJoin[NCLASS];
+    cudaStream_t classStream[MAXCLASS];
+    cudaEvent_t evFork, evJoin[MAXCLASS];
     int64_t nlaunch;             // kernels launched so far
     // RR_GRAPH: the captured launch sequence and the call it belongs to
     cudaStream_t capStream;
@@ -155,7 +158,7 @@ static int ensure_ws(rr_ctx *ctx, int count)
     CUDA_TRY(cudaMalloc(&ctx->d_ws, sizeof(JobWS) * (size_t)cap));
     if (ctx->d_classList) CUDA_TRY(cudaFree(ctx->d_classList));
     ctx->d_classList = nullptr;
-    CUDA_TRY(cudaMalloc(&ctx->d_classList, sizeof(int) * (size_t)cap * rr_ctx::NCLASS));
+    CUDA_TRY(cudaMalloc(&ctx->d_classList, sizeof(int) * (size_t)cap * rr_ctx::MAXCLASS));
     ctx->ws_cap = cap;
     return RR_OK;
 }
@@ -168,6 +171,8 @@ extern "C" int rr_ctx_create(rr_ctx **out, int64_t arena_bytes)
     ctx = new (std::nothrow) rr_ctx();
     if (!ctx) return fail(nullptr, RR_ERR_ARG, "rr_ctx_create: out of host memory");
     std::memset(ctx, 0, sizeof(*ctx));
+    ctx->nclass = 4;
+    ctx->shift = 0;
     if (arena_bytes <= 0) arena_bytes = 1ll << 30;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->arena, (size_t)arena_bytes);
@@ -186,12 +191,19 @@ extern "C" int rr_ctx_create(rr_ctx **out, int64_t arena_bytes)
     if (st != RR_OK) { rr_ctx_destroy(ctx); return st; }
     st = ensure_ws(ctx, 1);
     if (st != RR_OK) { rr_ctx_destroy(ctx); return st; }
-    bool ok = cudaMalloc(&ctx->d_classCount, sizeof(int) * rr_ctx::NCLASS) == cudaSuccess &&
+    bool ok = cudaMalloc(&ctx->d_classCount, sizeof(int) * rr_ctx::MAXCLASS) == cudaSuccess &&
               cudaEventCreateWithFlags(&ctx->evFork, cudaEventDisableTiming) == cudaSuccess &&
               cudaStreamCreateWithFlags(&ctx->capStream, cudaStreamNonBlocking) == cudaSuccess;
-    for (int c = 0; ok && c < rr_ctx::NCLASS; ++c)
-        ok = cudaStreamCreateWithFlags(&ctx->classStream[c], cudaStreamNonBlocking) == cudaSuccess &&
+    // class streams get priorities by class, the largest grids highest: their
+    // simulations are the longest, so their blocks should start first (this
+    // also holds inside a captured graph, instantiated with node priorities)
+    int least = 0, greatest = 0;
+    ok = ok && cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess;
+    for (int c = 0; ok && c < rr_ctx::MAXCLASS; ++c) {
+        const int prio = least + (greatest - least) * c / (rr_ctx::MAXCLASS - 1);
+        ok = cudaStreamCreateWithPriority(&ctx->classStream[c], cudaStreamNonBlocking, prio) == cudaSuccess &&
              cudaEventCreateWithFlags(&ctx->evJoin[c], cudaEventDisableTiming) == cudaSuccess;
+    }
     if (!ok) { rr_ctx_destroy(ctx); return fail(nullptr, RR_ERR_CUDA, "rr_ctx_create: stream/event setup failed"); }
     *out = ctx;
     return RR_OK;
@@ -209,7 +221,7 @@ extern "C" int rr_ctx_destroy(rr_ctx *ctx)
     cudaFree(ctx->d_classCount);
     cudaFree(ctx->d_classList);
     if (ctx->evFork) cudaEventDestroy(ctx->evFork);
-    for (int c = 0; c < rr_ctx::NCLASS; ++c) {
+    for (int c = 0; c < rr_ctx::MAXCLASS; ++c) {
         if (ctx->classStream[c]) cudaStreamDestroy(ctx->classStream[c]);
         if (ctx->evJoin[c]) cudaEventDestroy(ctx->evJoin[c]);
     }
@@ -238,14 +250,17 @@ static Arena arena_of(rr_ctx *ctx)
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// Blocks a launch may spread over all grids of a call (divided by the count).
+static int budget(const rr_ctx *ctx, int base) { return ctx->shift >= 0 ? base << ctx->shift : base >> -ctx->shift; }
+
 // Planning kernels over `count` device descriptors whose sides are <= max_side.
 static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, cudaStream_t s)
 {
     const Arena A = arena_of(ctx);
-    const int colBlocks = clampi(std::max(1, 4096 / count), 1, (max_side + 7) / 8);
+    const int colBlocks = clampi(std::max(1, budget(ctx, 4096) / count), 1, (max_side + 7) / 8);
     const int tiles = ((max_side + 31) / 32) * ((max_side + 31) / 32);
-    const int trBlocks = clampi(std::max(1, 4096 / count), 1, (tiles + 7) / 8);
-    const int recvBlocks = clampi(std::max(1, 2048 / count), 1, max_side);
+    const int trBlocks = clampi(std::max(1, budget(ctx, 4096) / count), 1, (tiles + 7) / 8);
+    const int recvBlocks = clampi(std::max(1, budget(ctx, 2048) / count), 1, max_side);
     mark(ctx, s, "k_plan_setup");
     k_plan_setup<<<(count + 127) / 128, 128, 0, s>>>(d_inst, ctx->d_ws, count, max_side, A);
     mark(ctx, s, "k_transpose");
@@ -268,13 +283,13 @@ static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side
 static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, cudaStream_t s)
 {
     const Arena A = arena_of(ctx);
-    const int pathBlocks = clampi(std::max(1, 8192 / count), 1, 512);
-    const int cellBlocks = clampi(std::max(1, 8192 / count), 1, (max_side * max_side + 255) / 256);
+    const int pathBlocks = clampi(std::max(1, budget(ctx, 8192) / count), 1, 512);
+    const int cellBlocks = clampi(std::max(1, budget(ctx, 8192) / count), 1, (max_side * max_side + 255) / 256);
     mark(ctx, s, "k_bsetup");
     k_bsetup<<<count, 512, 0, s>>>(d_inst, ctx->d_ws, count, A);
     {
         // Gamma by column and row sweeps (per-vertex lists only where they fail)
-        const int lineBlocks = clampi(std::max(1, 8192 / count), 1, (2 * max_side + 7) / 8);
+        const int lineBlocks = clampi(std::max(1, budget(ctx, 8192) / count), 1, (2 * max_side + 7) / 8);
         mark(ctx, s, "k_gcount");
         k_gcount<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
         mark(ctx, s, "k_gscan");
@@ -311,12 +326,12 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
     // streams so that each class's shared memory fits its own grids; slot
     // table, static lists and buffers live in shared memory (layout mirrored
     // in k_sim)
-    CUDA_TRY(cudaMemsetAsync(ctx->d_classCount, 0, sizeof(int) * rr_ctx::NCLASS, s));
+    CUDA_TRY(cudaMemsetAsync(ctx->d_classCount, 0, sizeof(int) * rr_ctx::MAXCLASS, s));
     // size classes, each launched on a stream of its own so that each gets
     // shared memory for its own sides; a call over a few grids uses one
     // class on the caller's stream (nothing to gain from the fork, and every
     // extra stream shares the device's few hardware queues with the others)
-    const int nclass = count <= SMALL_CALL ? 1 : rr_ctx::NCLASS;
+    const int nclass = count <= SMALL_CALL ? 1 : ctx->nclass;
     mark(ctx, s, "k_classify");
     k_classify<<<(count + 255) / 256, 256, 0, s>>>(d_inst, count, nclass, max_side, ctx->d_classCount,
                                                   ctx->d_classList);
@@ -449,7 +464,7 @@ extern "C" int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int 
         if (st == RR_OK && e != cudaSuccess)
             st = fail(ctx, RR_ERR_CUDA, "rr_plan_batched: graph capture: %s", cudaGetErrorString(e));
         if (st == RR_OK) {
-            const cudaError_t e2 = cudaGraphInstantiate(&ctx->graph, g, 0);
+            const cudaError_t e2 = cudaGraphInstantiate(&ctx->graph, g, cudaGraphInstantiateFlagUseNodePriority);
             if (e2 != cudaSuccess) {
                 ctx->graph = nullptr;
                 st = fail(ctx, RR_ERR_CUDA, "rr_plan_batched: graph instantiate: %s", cudaGetErrorString(e2));
@@ -467,6 +482,49 @@ extern "C" int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int 
     CUDA_TRY(cudaGraphLaunch(ctx->graph, stream));
     ctx->nlaunch += ctx->gLaunches;
     return RR_OK;
+}
+
+extern "C" int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
+                           cudaStream_t stream, int32_t *nclass, int32_t *shift)
+{
+    if (!ctx || !d_inst || count < 1 || count > 65535 || max_side < 1 || max_side > RR_MAX_SIDE ||
+        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY)))
+        return fail(ctx, RR_ERR_ARG, "rr_autotune: bad argument (count=%d max_side=%d flags=%d)", count, max_side,
+                    flags);
+    int st = ensure_ws(ctx, count);
+    if (st != RR_OK) return st;
+    static const int NC[3] = {2, 4, 8}, SH[3] = {-1, 0, 1};
+    cudaEvent_t a = nullptr, b = nullptr;
+    CUDA_TRY(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return fail(ctx, RR_ERR_CUDA, "rr_autotune: event"); }
+    const int tracing = ctx->tracing;
+    ctx->tracing = 0;
+    float best = 1e30f;
+    int bestN = ctx->nclass, bestS = ctx->shift;
+    for (int i = 0; i < 9 && st == RR_OK; ++i) {
+        ctx->nclass = NC[i / 3];
+        ctx->shift = SH[i % 3];
+        float t = 1e30f;
+        for (int rep = 0; rep < 2 && st == RR_OK; ++rep) {     // best of two
+            cudaEventRecord(a, stream);
+            st = launch_sequence(ctx, d_inst, count, max_side, flags, stream);
+            cudaEventRecord(b, stream);
+            if (st == RR_OK && cudaEventSynchronize(b) != cudaSuccess)
+                st = fail(ctx, RR_ERR_CUDA, "rr_autotune: %s", cudaGetErrorString(cudaGetLastError()));
+            float ms = 0.f;
+            if (st == RR_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) t = std::min(t, ms);
+        }
+        if (t < best) { best = t; bestN = ctx->nclass; bestS = ctx->shift; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->tracing = tracing;
+    ctx->nclass = bestN;
+    ctx->shift = bestS;
+    drop_graph(ctx);                     // captured under another configuration
+    if (nclass) *nclass = bestN;
+    if (shift) *shift = bestS;
+    return st;
 }
 
 // Library-internal: size a context's descriptor table for `count` instances

@@ -271,6 +271,44 @@ def test_batched_graph_replay(planner):
     assert counts[0] == counts[1] > 0
 
 
+def test_autotune_then_batched(planner):
+    """rr_autotune picks one of its configurations and leaves correct results;
+    a later call under the tuned configuration is correct too."""
+    import paper_2504_06182_gb300 as rr
+    from paper_2504_06182_gb300.planner import pack_instances, unpack_instances
+    insts = gridgen.mixed_instances(12, 40)
+    refs = [oracle.plan(i.grid, i.rect) for i in insts]
+    entries, outs = [], []
+    for inst, ref in zip(insts, refs):
+        s = inst.grid.shape[0]
+        k = max(len(ref.moves), 1)
+        steps = max(1, int((np.abs(ref.moves[:, 0] - ref.moves[:, 2]) +
+                            np.abs(ref.moves[:, 1] - ref.moves[:, 3])).sum()) if len(ref.moves) else 1)
+        mv = torch.empty((k, 4), dtype=torch.int32, device="cuda")
+        ops = torch.empty((steps, 3), dtype=torch.int32, device="cuda")
+        mem = torch.empty((steps,), dtype=torch.int32, device="cuda")
+        entries.append(dict(grid=to_device(inst.grid, rr.RR_BITS32), layout=rr.RR_BITS32, m=s, n=s, rect=inst.rect,
+                            moves=mv, cap_moves=k, ops=ops, cap_ops=steps, members=mem, cap_members=steps))
+        outs.append((mv, ops, mem))
+    dev = pack_instances(entries)
+    nclass, shift = rr.rr_autotune(planner.ctx, dev, len(entries), 256, rr.RR_WITH_BATCH)
+    assert nclass in (2, 4, 8) and shift in (-1, 0, 1)
+    for call in range(2):
+        if call == 1:
+            assert rr.rr_plan_batched(planner.ctx, dev, len(entries), 256, rr.RR_WITH_BATCH) == rr.RR_OK
+        torch.cuda.synchronize()
+        res = unpack_instances(dev, len(entries))
+        for inst, ref, r, (mv, ops, mem) in zip(insts, refs, res, outs):
+            assert r.status == (rr.RR_OK if ref.status == 0 else rr.RR_INFEASIBLE)
+            assert r.n_moves == len(ref.moves)
+            if ref.status != 0:
+                continue
+            assert (mv[: r.n_moves].cpu().numpy() == ref.moves).all()
+            rops, rmem = oracle.batch(ref.moves, *inst.grid.shape)
+            assert (ops[: r.n_ops].cpu().numpy() == rops).all() and r.n_ops == len(rops)
+            assert (mem[: r.n_members].cpu().numpy() == rmem).all() and r.n_members == len(rmem)
+
+
 def test_grid_1024_bit_layout(planner):
     """Full-size 1024 x 1024 grid with a centred 720 x 720 target: the whole
     move list against the oracle, and the batches against the oracle (all of
