@@ -126,17 +126,29 @@ int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, i
                     cudaStream_t stream);
 
 /* Launch-configuration autotuner for rr_plan_batched (nothing in the paper
- * corresponds to it). Runs the call's launch sequence on these instances
- * under nine configurations: 2, 4 or 8 simulation size classes, times per-grid
- * block budgets of the planning and graph kernels scaled by 1/2, 1 or 2. Each
- * is timed with CUDA events on `stream`, best of two. The fastest is kept in
- * the context for later rr_plan_batched calls (any captured RR_GRAPH graph is
- * dropped), and written to *nclass and *shift (log2 of the budget scale) when
- * those are not NULL. Every configuration computes the same results, so the
- * descriptors and outputs hold this call's results afterwards. Synchronises;
- * flags as rr_plan_batched without RR_GRAPH. */
+ * corresponds to it). Runs the call's launch sequence on these instances,
+ * timed with CUDA events on `stream` (best of two each): first under nine
+ * configurations (2, 4 or 8 simulation size classes, times per-grid block
+ * budgets of the planning and graph kernels scaled by 1/2, 1 or 2), then,
+ * with the best of those, under four pipeline splits (see below): 0 none,
+ * 1 the largest quarter first, 2 the largest 1/16 then up to 1/4, 3 groups
+ * ending at 1/16, 1/8, 1/4 and 1/2. The fastest is kept in the context for
+ * later rr_plan_batched calls (a captured RR_GRAPH graph is dropped) and
+ * written to *nclass, *shift (log2 of the budget scale) and *pipe (the
+ * split) when those are not NULL. Every
+ * configuration computes the same results, so the descriptors and outputs
+ * hold this call's results afterwards. Synchronises; flags as
+ * rr_plan_batched without RR_GRAPH.
+ *
+ * Pipeline (batched calls with batching over at least 256 grids): the grids
+ * are ordered by side, largest first, into a descriptor copy; each leading
+ * group is planned, given its conflict graph and simulated on a stream of
+ * its own (priorities descending) while the rest is planned and given its
+ * graphs on a low-priority stream; each group's simulations start once the
+ * previous group's have started; per-grid outputs are then copied back into
+ * the caller's descriptors. The default is split 1. */
 int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
-                cudaStream_t stream, int32_t *nclass, int32_t *shift);
+                cudaStream_t stream, int32_t *nclass, int32_t *shift, int32_t *pipe);
 
 /* ------------------------------------------------------------------ serving
  * Continuous batching of planning requests (red-rec + batching per request):

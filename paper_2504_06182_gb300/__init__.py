@@ -97,7 +97,8 @@ def load(path: str = LIB_PATH):
     L.rr_stage_times.restype = I32
     L.rr_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     L.rr_launch_count.restype = I32
-    L.rr_autotune.argtypes = [P, P, I32, I32, I32, P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.rr_autotune.argtypes = [P, P, I32, I32, I32, P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(ctypes.c_int32)]
     L.rr_autotune.restype = I32
     L.rr_plan_noalloc.argtypes = [P, I32, I32, I32, rr_rect, P, I64, ctypes.POINTER(I64), P]
     L.rr_plan_noalloc.restype = I32
@@ -196,13 +197,13 @@ def rr_stage_times(ctx, cap: int = 32):
 
 def rr_autotune(ctx, d_inst, count, max_side, flags=RR_WITH_BATCH, stream=None):
     """Picks and keeps the fastest launch configuration for these instances.
-    Returns (size classes, log2 block-budget scale)."""
-    nc, sh = ctypes.c_int32(0), ctypes.c_int32(0)
+    Returns (size classes, log2 block-budget scale, pipeline split 0..3)."""
+    nc, sh, pd = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
     st = load().rr_autotune(ctx, _addr(d_inst), int(count), int(max_side), int(flags), _stream(stream),
-                            ctypes.byref(nc), ctypes.byref(sh))
+                            ctypes.byref(nc), ctypes.byref(sh), ctypes.byref(pd))
     if st != RR_OK:
         raise RRError(st, rr_last_error(ctx))
-    return int(nc.value), int(sh.value)
+    return int(nc.value), int(sh.value), int(pd.value)
 
 
 def rr_launch_count(ctx) -> int:

@@ -886,6 +886,53 @@ __device__ void dissolve(const Sim<IX> &X, int nm, bool rowLine)
     __syncwarp();
 }
 
+// Instance order by side, largest first: a counting sort on max(m, n)
+// (one block; positions within a side follow the atomics, which does not
+// matter: instances are independent). perm[i] is the instance at position i.
+__global__ void k_order(const rr_instance *inst, int count, int *perm)
+{
+    __shared__ int hist[RR_MAX_SIDE + 2];
+    for (int i = threadIdx.x; i < RR_MAX_SIDE + 2; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    auto key = [&](int q) { return RR_MAX_SIDE + 1 - min(max(max(inst[q].m, inst[q].n), 0), RR_MAX_SIDE + 1); };
+    for (int q = threadIdx.x; q < count; q += blockDim.x) atomicAdd(&hist[key(q)], 1);
+    __syncthreads();
+    if (threadIdx.x < 32) {              // exclusive scan, one warp
+        int carry = 0;
+        for (int b = 0; b < RR_MAX_SIDE + 2; b += 32) {
+            const int i = b + threadIdx.x;
+            const int v = i < RR_MAX_SIDE + 2 ? hist[i] : 0;
+            const int inc = warp_incl_scan(v);
+            if (i < RR_MAX_SIDE + 2) hist[i] = carry + inc - v;
+            carry += __shfl_sync(FULL, inc, 31);
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < count; q += blockDim.x) perm[atomicAdd(&hist[key(q)], 1)] = q;
+}
+
+// Descriptor copy in that order (one 128-byte descriptor per block).
+__global__ void k_gather(const rr_instance *inst, const int *perm, rr_instance *pinst)
+{
+    const int32_t *src = (const int32_t *)&inst[perm[blockIdx.x]];
+    int32_t *dst = (int32_t *)&pinst[blockIdx.x];
+    dst[threadIdx.x] = src[threadIdx.x];
+}
+
+// Per-instance outputs back to the caller's descriptors.
+__global__ void k_scatter(rr_instance *inst, const int *perm, const rr_instance *pinst, int count)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const rr_instance *p = &pinst[i];
+        rr_instance *o = &inst[perm[i]];
+        o->n_moves = p->n_moves;
+        o->n_steps = p->n_steps;
+        o->n_ops = p->n_ops;
+        o->n_members = p->n_members;
+        o->status = p->status;
+    }
+}
+
 // Instances grouped by size class (largest side <= classSide[c]) so that each
 // class's simulation launch gets shared memory sized for its own grids.
 __global__ void k_classify(rr_instance *inst, int count, int nclass, int max_side, int *classCount,
@@ -906,8 +953,11 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
                                          const int *classCount, int slotCap, int lineCap)
 {
     extern __shared__ int4 smem_i4[];
-    if ((int)blockIdx.x >= *classCount) return;
-    const int q = classList[blockIdx.x];
+    int q = blockIdx.x;                  // without a class list: every instance
+    if (classList) {
+        if ((int)blockIdx.x >= *classCount) return;
+        q = classList[blockIdx.x];
+    }
     if (q >= count) return;
     rr_instance *I = &inst[q];
     if (!live(I)) return;

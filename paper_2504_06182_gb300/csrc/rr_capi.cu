@@ -29,6 +29,9 @@ __global__ void k_bsort(rr_instance *, JobWS *, int);
 __global__ void k_bsucc(rr_instance *, JobWS *, int);
 __global__ void k_brec(rr_instance *, JobWS *, int);
 __global__ void k_classify(rr_instance *, int, int, int, int *, int *);
+__global__ void k_order(const rr_instance *, int, int *);
+__global__ void k_gather(const rr_instance *, const int *, rr_instance *);
+__global__ void k_scatter(rr_instance *, const int *, const rr_instance *, int);
 __global__ void k_sim16(rr_instance *, JobWS *, int, const int *, const int *, int, int);
 __global__ void k_sim32(rr_instance *, JobWS *, int, const int *, const int *, int, int);
 }  // namespace rrk
@@ -59,6 +62,15 @@ struct rr_ctx {
     // launch configuration of batched calls (rr_autotune may change it):
     // simulation size classes, and per-grid block budgets scaled by 2^shift
     int nclass = 4, shift = 0;
+    int pipe;                    // batched calls: pipeline split (index into PIPE_SPLITS; 0: none)
+    // pipeline by size: sorted descriptor copy; a stream per leading group
+    // (priorities descending) and one for the rest
+    static const int MAXLEAD = 4;
+    rr_instance *d_pinst;
+    int *d_perm;
+    cudaStream_t leadStream[MAXLEAD], restStream;
+    cudaEvent_t evStart, evLead[MAXLEAD], evRest, evSim[MAXLEAD];
+    int quiet;                   // no stage marks (the second pipeline)
     int *d_classCount, *d_classList;
     int classListCap;
     cudaStream_t classStream[MAXCLASS];
@@ -80,7 +92,7 @@ struct rr_ctx {
 
 static void mark(rr_ctx *ctx, cudaStream_t s, const char *name)
 {
-    if (!ctx->tracing || ctx->capturing || ctx->nmarks >= 32) return;
+    if (!ctx->tracing || ctx->capturing || ctx->quiet || ctx->nmarks >= 32) return;
     if (!ctx->marks[ctx->nmarks]) cudaEventCreate(&ctx->marks[ctx->nmarks]);
     cudaEventRecord(ctx->marks[ctx->nmarks], s);
     ctx->names[ctx->nmarks] = name;
@@ -159,6 +171,12 @@ static int ensure_ws(rr_ctx *ctx, int count)
     if (ctx->d_classList) CUDA_TRY(cudaFree(ctx->d_classList));
     ctx->d_classList = nullptr;
     CUDA_TRY(cudaMalloc(&ctx->d_classList, sizeof(int) * (size_t)cap * rr_ctx::MAXCLASS));
+    if (ctx->d_pinst) CUDA_TRY(cudaFree(ctx->d_pinst));
+    if (ctx->d_perm) CUDA_TRY(cudaFree(ctx->d_perm));
+    ctx->d_pinst = nullptr;
+    ctx->d_perm = nullptr;
+    CUDA_TRY(cudaMalloc(&ctx->d_pinst, sizeof(rr_instance) * (size_t)cap));
+    CUDA_TRY(cudaMalloc(&ctx->d_perm, sizeof(int) * (size_t)cap));
     ctx->ws_cap = cap;
     return RR_OK;
 }
@@ -173,6 +191,7 @@ extern "C" int rr_ctx_create(rr_ctx **out, int64_t arena_bytes)
     std::memset(ctx, 0, sizeof(*ctx));
     ctx->nclass = 4;
     ctx->shift = 0;
+    ctx->pipe = 1;
     if (arena_bytes <= 0) arena_bytes = 1ll << 30;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->arena, (size_t)arena_bytes);
@@ -199,6 +218,15 @@ extern "C" int rr_ctx_create(rr_ctx **out, int64_t arena_bytes)
     // also holds inside a captured graph, instantiated with node priorities)
     int least = 0, greatest = 0;
     ok = ok && cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&ctx->restStream, cudaStreamNonBlocking, least) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ctx->evStart, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ctx->evRest, cudaEventDisableTiming) == cudaSuccess;
+    for (int g = 0; ok && g < rr_ctx::MAXLEAD; ++g) {
+        const int prio = greatest + (least - greatest) * g / rr_ctx::MAXLEAD;
+        ok = cudaStreamCreateWithPriority(&ctx->leadStream[g], cudaStreamNonBlocking, prio) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ctx->evLead[g], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ctx->evSim[g], cudaEventDisableTiming) == cudaSuccess;
+    }
     for (int c = 0; ok && c < rr_ctx::MAXCLASS; ++c) {
         const int prio = least + (greatest - least) * c / (rr_ctx::MAXCLASS - 1);
         ok = cudaStreamCreateWithPriority(&ctx->classStream[c], cudaStreamNonBlocking, prio) == cudaSuccess &&
@@ -218,6 +246,15 @@ extern "C" int rr_ctx_destroy(rr_ctx *ctx)
     cudaFree(ctx->d_ws);
     drop_graph(ctx);
     if (ctx->capStream) cudaStreamDestroy(ctx->capStream);
+    if (ctx->restStream) cudaStreamDestroy(ctx->restStream);
+    for (cudaEvent_t e : {ctx->evStart, ctx->evRest}) if (e) cudaEventDestroy(e);
+    for (int g = 0; g < rr_ctx::MAXLEAD; ++g) {
+        if (ctx->leadStream[g]) cudaStreamDestroy(ctx->leadStream[g]);
+        if (ctx->evLead[g]) cudaEventDestroy(ctx->evLead[g]);
+        if (ctx->evSim[g]) cudaEventDestroy(ctx->evSim[g]);
+    }
+    cudaFree(ctx->d_pinst);
+    cudaFree(ctx->d_perm);
     cudaFree(ctx->d_classCount);
     cudaFree(ctx->d_classList);
     if (ctx->evFork) cudaEventDestroy(ctx->evFork);
@@ -254,7 +291,7 @@ static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v
 static int budget(const rr_ctx *ctx, int base) { return ctx->shift >= 0 ? base << ctx->shift : base >> -ctx->shift; }
 
 // Planning kernels over `count` device descriptors whose sides are <= max_side.
-static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, cudaStream_t s)
+static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, int max_side, cudaStream_t s)
 {
     const Arena A = arena_of(ctx);
     const int colBlocks = clampi(std::max(1, budget(ctx, 4096) / count), 1, (max_side + 7) / 8);
@@ -262,84 +299,95 @@ static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side
     const int trBlocks = clampi(std::max(1, budget(ctx, 4096) / count), 1, (tiles + 7) / 8);
     const int recvBlocks = clampi(std::max(1, budget(ctx, 2048) / count), 1, max_side);
     mark(ctx, s, "k_plan_setup");
-    k_plan_setup<<<(count + 127) / 128, 128, 0, s>>>(d_inst, ctx->d_ws, count, max_side, A);
+    k_plan_setup<<<(count + 127) / 128, 128, 0, s>>>(d_inst, ws, count, max_side, A);
     mark(ctx, s, "k_transpose");
-    k_transpose<<<dim3(trBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    k_transpose<<<dim3(trBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_colstats");
-    k_colstats<<<dim3(colBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    k_colstats<<<dim3(colBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     const size_t pairSmem = (size_t)max_side * 30 + 64;
     mark(ctx, s, "k_pair");
-    k_pair<<<count, 32, pairSmem, s>>>(d_inst, ctx->d_ws, count);
+    k_pair<<<count, 32, pairSmem, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_emit_cols");
-    k_emit_cols<<<dim3(colBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    k_emit_cols<<<dim3(colBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_emit_recv");
-    k_emit_recv<<<dim3(recvBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    k_emit_recv<<<dim3(recvBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, nullptr);
     CUDA_TRY(cudaGetLastError());
     ctx->nlaunch += 6;
     return RR_OK;
 }
 
-static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, cudaStream_t s)
+// Simulation launch shapes: per size class on forked streams, or one launch
+// over every instance of the call on its stream.
+enum { SIM_CLASSES = 0, SIM_ONE = 1 };
+
+// Batching kernels. Before the simulation the stream waits for `waitSim`
+// and records `atSim` (either may be null).
+static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, int max_side, cudaStream_t s,
+                        int simMode, cudaEvent_t waitSim, cudaEvent_t atSim)
 {
     const Arena A = arena_of(ctx);
     const int pathBlocks = clampi(std::max(1, budget(ctx, 8192) / count), 1, 512);
     const int cellBlocks = clampi(std::max(1, budget(ctx, 8192) / count), 1, (max_side * max_side + 255) / 256);
     mark(ctx, s, "k_bsetup");
-    k_bsetup<<<count, 512, 0, s>>>(d_inst, ctx->d_ws, count, A);
+    k_bsetup<<<count, 512, 0, s>>>(d_inst, ws, count, A);
     {
         // Gamma by column and row sweeps (per-vertex lists only where they fail)
         const int lineBlocks = clampi(std::max(1, budget(ctx, 8192) / count), 1, (2 * max_side + 7) / 8);
         mark(ctx, s, "k_gcount");
-        k_gcount<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+        k_gcount<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ws, count);
         mark(ctx, s, "k_gscan");
-        k_gscan<<<count, 64, 0, s>>>(d_inst, ctx->d_ws, count);
+        k_gscan<<<count, 64, 0, s>>>(d_inst, ws, count);
         mark(ctx, s, "k_gfill");
-        k_gfill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+        k_gfill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ws, count);
         int P2 = 32;
         while (P2 < max_side) P2 <<= 1;
         if (8 * 4 * P2 > ctx->smemLimit[SM_GSORT] || 8 * 4 * max_side > ctx->smemLimit[SM_GSWEEP_H] ||
             8 * 8 * max_side > ctx->smemLimit[SM_GSWEEP_V])
             return fail(ctx, RR_ERR_ARG, "Gamma sweeps: shared memory for side %d too large", max_side);
         mark(ctx, s, "k_gsort");
-        k_gsort<<<dim3(lineBlocks, count), 256, 8 * 4 * (size_t)P2, s>>>(d_inst, ctx->d_ws, count, P2);
+        k_gsort<<<dim3(lineBlocks, count), 256, 8 * 4 * (size_t)P2, s>>>(d_inst, ws, count, P2);
         mark(ctx, s, "k_gsweep_h");
-        k_gsweep_h<<<dim3(lineBlocks, count), 256, 8 * 4 * (size_t)max_side, s>>>(d_inst, ctx->d_ws, count, max_side);
+        k_gsweep_h<<<dim3(lineBlocks, count), 256, 8 * 4 * (size_t)max_side, s>>>(d_inst, ws, count, max_side);
         mark(ctx, s, "k_gsweep_v");
-        k_gsweep_v<<<dim3(lineBlocks, count), 256, 8 * 8 * (size_t)max_side, s>>>(d_inst, ctx->d_ws, count, max_side);
+        k_gsweep_v<<<dim3(lineBlocks, count), 256, 8 * 8 * (size_t)max_side, s>>>(d_inst, ws, count, max_side);
         mark(ctx, s, "k_galloc");
-        k_galloc<<<count, 256, 0, s>>>(d_inst, ctx->d_ws, count, A);
+        k_galloc<<<count, 256, 0, s>>>(d_inst, ws, count, A);
     }
     mark(ctx, s, "k_bcount");
-    k_bcount<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    k_bcount<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_bscan_cells");
-    k_bscan_cells<<<count, 1024, 0, s>>>(d_inst, ctx->d_ws, count);
+    k_bscan_cells<<<count, 1024, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_bfill");
-    k_bfill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    k_bfill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_bsort");
-    k_bsort<<<dim3(cellBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    k_bsort<<<dim3(cellBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_bsucc");
-    k_bsucc<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    k_bsucc<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_brec");
-    k_brec<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ctx->d_ws, count);
+    k_brec<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     // simulation: one warp per instance, launched per size class on forked
     // streams so that each class's shared memory fits its own grids; slot
     // table, static lists and buffers live in shared memory (layout mirrored
     // in k_sim)
-    CUDA_TRY(cudaMemsetAsync(ctx->d_classCount, 0, sizeof(int) * rr_ctx::MAXCLASS, s));
-    // size classes, each launched on a stream of its own so that each gets
-    // shared memory for its own sides; a call over a few grids uses one
-    // class on the caller's stream (nothing to gain from the fork, and every
-    // extra stream shares the device's few hardware queues with the others)
-    const int nclass = count <= SMALL_CALL ? 1 : ctx->nclass;
-    mark(ctx, s, "k_classify");
-    k_classify<<<(count + 255) / 256, 256, 0, s>>>(d_inst, count, nclass, max_side, ctx->d_classCount,
-                                                  ctx->d_classList);
+    // one launch over all instances (a small call, or the largest grids of a
+    // pipelined call), or size classes each on a stream of its own so that
+    // each gets shared memory for its own sides
+    const bool one = simMode == SIM_ONE || count <= SMALL_CALL;
+    const int nclass = one ? 1 : ctx->nclass;
+    if (!one) {
+        CUDA_TRY(cudaMemsetAsync(ctx->d_classCount, 0, sizeof(int) * rr_ctx::MAXCLASS, s));
+        mark(ctx, s, "k_classify");
+        k_classify<<<(count + 255) / 256, 256, 0, s>>>(d_inst, count, nclass, max_side, ctx->d_classCount,
+                                                      ctx->d_classList);
+    }
+    if (waitSim) CUDA_TRY(cudaStreamWaitEvent(s, waitSim, 0));
+    if (atSim) CUDA_TRY(cudaEventRecord(atSim, s));
     mark(ctx, s, "k_sim");
-    if (nclass > 1) CUDA_TRY(cudaEventRecord(ctx->evFork, s));
+    if (!one) CUDA_TRY(cudaEventRecord(ctx->evFork, s));
     for (int c = nclass - 1; c >= 0; --c) {
-        cudaStream_t cs = nclass > 1 ? ctx->classStream[c] : s;
-        if (nclass > 1) CUDA_TRY(cudaStreamWaitEvent(cs, ctx->evFork, 0));
+        cudaStream_t cs = one ? s : ctx->classStream[c];
+        if (!one) CUDA_TRY(cudaStreamWaitEvent(cs, ctx->evFork, 0));
         const int side = class_side(max_side, c, nclass);
         // ready moves never exceed two per column here (one chain head each
         // way); beyond the capacity slots spill to the global overflow area
@@ -351,21 +399,18 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, int count, int max_sid
         const size_t simSmem = sim_smem_bytes(slotCap, lineCap, narrow ? 2 : 4);
         if (simSmem > (size_t)ctx->smemLimit[narrow ? SM_SIM16 : SM_SIM32])
             return fail(ctx, RR_ERR_ARG, "simulation shared memory %zu too large", simSmem);
-        if (narrow) {
-            k_sim16<<<count, 32, simSmem, cs>>>(d_inst, ctx->d_ws, count, ctx->d_classList + (size_t)c * count,
-                                                      ctx->d_classCount + c, slotCap, lineCap);
-        } else {
-            k_sim32<<<count, 32, simSmem, cs>>>(d_inst, ctx->d_ws, count, ctx->d_classList + (size_t)c * count,
-                                                      ctx->d_classCount + c, slotCap, lineCap);
-        }
-        if (nclass > 1) {
+        const int *list = one ? nullptr : ctx->d_classList + (size_t)c * count;
+        const int *cnt = one ? nullptr : ctx->d_classCount + c;
+        if (narrow) k_sim16<<<count, 32, simSmem, cs>>>(d_inst, ws, count, list, cnt, slotCap, lineCap);
+        else k_sim32<<<count, 32, simSmem, cs>>>(d_inst, ws, count, list, cnt, slotCap, lineCap);
+        if (!one) {
             CUDA_TRY(cudaEventRecord(ctx->evJoin[c], cs));
             CUDA_TRY(cudaStreamWaitEvent(s, ctx->evJoin[c], 0));
         }
     }
     mark(ctx, s, nullptr);
     CUDA_TRY(cudaGetLastError());
-    ctx->nlaunch += 15 + nclass;
+    ctx->nlaunch += (one ? 14 : 15) + nclass;
     return RR_OK;
 }
 
@@ -389,7 +434,7 @@ extern "C" int rr_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n
     ctx->nmarks = 0;
     CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->d_one, &h, sizeof(h), cudaMemcpyHostToDevice, stream));
-    int st = launch_plan(ctx, ctx->d_one, 1, std::max(m, n), stream);
+    int st = launch_plan(ctx, ctx->d_one, ctx->d_ws, 1, std::max(m, n), stream);
     if (st != RR_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(&h, ctx->d_one, sizeof(h), cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaStreamSynchronize(stream));
@@ -415,7 +460,7 @@ extern "C" int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, in
     ctx->nmarks = 0;
     CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->d_one, &h, sizeof(h), cudaMemcpyHostToDevice, stream));
-    int st = launch_batch(ctx, ctx->d_one, 1, std::max(m, n), stream);
+    int st = launch_batch(ctx, ctx->d_one, ctx->d_ws, 1, std::max(m, n), stream, SIM_ONE, nullptr, nullptr);
     if (st != RR_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(&h, ctx->d_one, sizeof(h), cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaStreamSynchronize(stream));
@@ -425,16 +470,85 @@ extern "C" int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, in
     return h.status;
 }
 
+// Calls over at least this many grids, with batching, may run pipelined.
+static constexpr int PIPE_MIN = 256;
+// Pipeline splits: the leading groups end at these fractions of the grids
+// (ordered by side, largest first); the rest forms the last group.
+static constexpr int PIPE_SPLITS = 4;
+static const int PIPE_FRAC16[PIPE_SPLITS][rr_ctx::MAXLEAD] = {
+    {0, 0, 0, 0},          // none
+    {4, 0, 0, 0},          // the largest quarter, then the rest
+    {1, 4, 0, 0},          // 1/16, 1/4
+    {1, 2, 4, 8},          // 1/16, 1/8, 1/4, 1/2
+};
+
 // The whole sequence of one rr_plan_batched call on `stream`.
+//
+// With batching, a call over many grids can run pipelined by size: the
+// grids are ordered by side, largest first, into a descriptor copy; each
+// leading group is planned, given its conflict graph and simulated (one
+// launch) on a stream of its own, priorities descending, and the rest goes
+// through planning and graph construction meanwhile on a low-priority stream
+// and is simulated by size class. A group's simulations start once the
+// previous group's have started, so the largest grids, whose simulations
+// are the longest, start first instead of after every grid's graph.
 static int launch_sequence(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
                            cudaStream_t stream)
 {
     CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
-    if (flags & RR_BATCH_ONLY) return launch_batch(ctx, d_inst, count, max_side, stream);
-    int st = launch_plan(ctx, d_inst, count, max_side, stream);
+    const bool plan = !(flags & RR_BATCH_ONLY), batch = (flags & (RR_WITH_BATCH | RR_BATCH_ONLY)) != 0;
+    const int *frac = PIPE_FRAC16[ctx->pipe > 0 && ctx->pipe < PIPE_SPLITS ? ctx->pipe : 0];
+    if (!batch || frac[0] == 0 || count < PIPE_MIN) {
+        int st = plan ? launch_plan(ctx, d_inst, ctx->d_ws, count, max_side, stream) : RR_OK;
+        if (st == RR_OK && batch)
+            st = launch_batch(ctx, d_inst, ctx->d_ws, count, max_side, stream, SIM_CLASSES, nullptr, nullptr);
+        return st;
+    }
+    mark(ctx, stream, "k_order");
+    k_order<<<1, 1024, 0, stream>>>(d_inst, count, ctx->d_perm);
+    mark(ctx, stream, "k_gather");
+    k_gather<<<count, 32, 0, stream>>>(d_inst, ctx->d_perm, ctx->d_pinst);
+    CUDA_TRY(cudaEventRecord(ctx->evStart, stream));
+    int st = RR_OK, lo = 0, ng = 0;
+    cudaEvent_t prevSim = nullptr;
+    for (int g = 0; g < rr_ctx::MAXLEAD && frac[g] && st == RR_OK; ++g) {
+        const int hi = std::max(lo + 1, (int)((int64_t)count * frac[g] / 16));
+        if (hi >= count) break;
+        cudaStream_t gs = ctx->leadStream[g];
+        CUDA_TRY(cudaStreamWaitEvent(gs, ctx->evStart, 0));
+        ctx->quiet = g > 0;                  // stage marks follow the first group
+        if (plan) st = launch_plan(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, hi - lo, max_side, gs);
+        if (st == RR_OK)
+            st = launch_batch(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, hi - lo, max_side, gs, SIM_ONE, prevSim,
+                              ctx->evSim[g]);
+        // the "k_sim" stage runs on to the join after every simulation (drop
+        // the first group's end-of-sequence mark)
+        if (g == 0 && ctx->nmarks > 0 && !ctx->names[ctx->nmarks - 1]) --ctx->nmarks;
+        if (st == RR_OK) st = cudaEventRecord(ctx->evLead[g], gs) == cudaSuccess ? RR_OK : fail(ctx, RR_ERR_CUDA, "record");
+        prevSim = ctx->evSim[g];
+        lo = hi;
+        ++ng;
+    }
+    ctx->quiet = 1;
+    if (st == RR_OK) {
+        cudaStream_t rs = ctx->restStream;
+        CUDA_TRY(cudaStreamWaitEvent(rs, ctx->evStart, 0));
+        if (plan) st = launch_plan(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, count - lo, max_side, rs);
+        if (st == RR_OK)
+            st = launch_batch(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, count - lo, max_side, rs, SIM_CLASSES, prevSim,
+                              nullptr);
+        if (st == RR_OK) st = cudaEventRecord(ctx->evRest, rs) == cudaSuccess ? RR_OK : fail(ctx, RR_ERR_CUDA, "record");
+    }
+    ctx->quiet = 0;
     if (st != RR_OK) return st;
-    if (flags & RR_WITH_BATCH) st = launch_batch(ctx, d_inst, count, max_side, stream);
-    return st;
+    for (int g = 0; g < ng; ++g) CUDA_TRY(cudaStreamWaitEvent(stream, ctx->evLead[g], 0));
+    CUDA_TRY(cudaStreamWaitEvent(stream, ctx->evRest, 0));
+    mark(ctx, stream, "k_scatter");
+    k_scatter<<<(count + 255) / 256, 256, 0, stream>>>(d_inst, ctx->d_perm, ctx->d_pinst, count);
+    mark(ctx, stream, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    ctx->nlaunch += 3;
+    return RR_OK;
 }
 
 extern "C" int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
@@ -485,7 +599,7 @@ extern "C" int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int 
 }
 
 extern "C" int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
-                           cudaStream_t stream, int32_t *nclass, int32_t *shift)
+                           cudaStream_t stream, int32_t *nclass, int32_t *shift, int32_t *pipe)
 {
     if (!ctx || !d_inst || count < 1 || count > 65535 || max_side < 1 || max_side > RR_MAX_SIDE ||
         (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY)))
@@ -516,6 +630,26 @@ extern "C" int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
         }
         if (t < best) { best = t; bestN = ctx->nclass; bestS = ctx->shift; }
     }
+    // then the pipeline split under that configuration
+    ctx->nclass = bestN;
+    ctx->shift = bestS;
+    int bestP = ctx->pipe;
+    best = 1e30f;
+    for (int i = 0; i < PIPE_SPLITS && st == RR_OK; ++i) {
+        ctx->pipe = i;
+        float t = 1e30f;
+        for (int rep = 0; rep < 2 && st == RR_OK; ++rep) {
+            cudaEventRecord(a, stream);
+            st = launch_sequence(ctx, d_inst, count, max_side, flags, stream);
+            cudaEventRecord(b, stream);
+            if (st == RR_OK && cudaEventSynchronize(b) != cudaSuccess)
+                st = fail(ctx, RR_ERR_CUDA, "rr_autotune: %s", cudaGetErrorString(cudaGetLastError()));
+            float ms = 0.f;
+            if (st == RR_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) t = std::min(t, ms);
+        }
+        if (t < best) { best = t; bestP = ctx->pipe; }
+    }
+    ctx->pipe = bestP;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     ctx->tracing = tracing;
@@ -524,6 +658,7 @@ extern "C" int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
     drop_graph(ctx);                     // captured under another configuration
     if (nclass) *nclass = bestN;
     if (shift) *shift = bestS;
+    if (pipe) *pipe = bestP;
     return st;
 }
 
