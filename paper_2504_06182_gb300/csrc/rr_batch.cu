@@ -591,7 +591,14 @@ template <typename IX> struct SlotSoA {
     // the leader and the members ever finish
 };
 
-template <typename IX> struct Sim {
+// The narrow simulation (WIDE false) keeps every slot in shared memory and
+// gives up on an instance that needs more (it is retried by the wide one);
+// the wide simulation spills slots beyond the shared capacity C to a global
+// overflow area. Peak demand on red-rec plans is two ready moves per column
+// (one chain head per vertical direction), within the shared capacity.
+template <typename IX, bool WIDE> struct Sim {
+    using ix = IX;
+    static constexpr bool wide = WIDE;
     SlotSoA<IX> sm, gm;
     int C, m, n, Wm, Wn;
     int16_t *freeStk;
@@ -617,8 +624,15 @@ template <typename T> struct SlotRef {
         return *this;
     }
 };
-#define SLOTF(X, f, i) \
-    (SlotRef<std::remove_reference_t<decltype(*(X).sm.f)>>{(X).sm.f, (X).gm.f, (int)(i), (X).C})
+template <bool WIDE, typename T> struct SlotAt {
+    static __device__ __forceinline__ T &at(T *s, T *, int i, int) { return s[i]; }
+};
+template <typename T> struct SlotAt<true, T> {
+    static __device__ __forceinline__ SlotRef<T> at(T *s, T *g, int i, int C) { return SlotRef<T>{s, g, i, C}; }
+};
+#define SLOTF(X, f, i)                                                                         \
+    (SlotAt<std::decay_t<decltype(X)>::wide, std::remove_reference_t<decltype(*(X).sm.f)>>::at( \
+        (X).sm.f, (X).gm.f, (int)(i), (X).C))
 
 __device__ __forceinline__ int key_of(int r, int c, int d) { return r | (c << 10) | (d << 20) | KEY_LIVE; }
 __device__ __forceinline__ int key_r(int k) { return k & 1023; }
@@ -642,9 +656,10 @@ __device__ __forceinline__ int warp_min(int v)
     return v;
 }
 
-template <typename IX>
-__device__ __forceinline__ void bits_set(const Sim<IX> &X, int d, int r, int c)
+template <class S>
+__device__ __forceinline__ void bits_set(const S &X, int d, int r, int c)
 {
+    using IX = typename S::ix;
     if (d < 2) atomicOr(&X.rowBits[d * X.Wm + (r >> 5)], 1u << (r & 31));
     else atomicOr(&X.colBits[(d - 2) * X.Wn + (c >> 5)], 1u << (c & 31));
 }
@@ -652,36 +667,40 @@ __device__ __forceinline__ void bits_set(const Sim<IX> &X, int d, int r, int c)
 // Static-list maintenance. push/remove touch the row list and the column
 // list of the slot's current key; callers that run them on several lanes at
 // once must guarantee distinct lists (see dissolve()).
-template <typename IX>
-__device__ void push_row(const Sim<IX> &X, int si, int key)
+template <class S>
+__device__ void push_row(const S &X, int si, int key)
 {
+    using IX = typename S::ix;
     IX *h = &X.rowHead[key_d(key) * X.m + key_r(key)];
     SLOTF(X, rp, si) = (IX)-1; SLOTF(X, rn, si) = *h;
     if (*h >= 0) SLOTF(X, rp, *h) = (IX)si;
     *h = (IX)si;
     if (key_d(key) < 2) atomicOr(&X.rowBits[key_d(key) * X.Wm + (key_r(key) >> 5)], 1u << (key_r(key) & 31));
 }
-template <typename IX>
-__device__ void push_col(const Sim<IX> &X, int si, int key)
+template <class S>
+__device__ void push_col(const S &X, int si, int key)
 {
+    using IX = typename S::ix;
     IX *h = &X.colHead[key_d(key) * X.n + key_c(key)];
     SLOTF(X, cp, si) = (IX)-1; SLOTF(X, cn, si) = *h;
     if (*h >= 0) SLOTF(X, cp, *h) = (IX)si;
     *h = (IX)si;
     if (key_d(key) >= 2) atomicOr(&X.colBits[(key_d(key) - 2) * X.Wn + (key_c(key) >> 5)], 1u << (key_c(key) & 31));
 }
-template <typename IX>
-__device__ void unlink_row(const Sim<IX> &X, int si, int key)
+template <class S>
+__device__ void unlink_row(const S &X, int si, int key)
 {
+    using IX = typename S::ix;
     const int p = SLOTF(X, rp, si), q = SLOTF(X, rn, si);
     IX *h = &X.rowHead[key_d(key) * X.m + key_r(key)];
     if (p >= 0) SLOTF(X, rn, p) = (IX)q; else *h = (IX)q;
     if (q >= 0) SLOTF(X, rp, q) = (IX)p;
     if (*h < 0 && key_d(key) < 2) atomicAnd(&X.rowBits[key_d(key) * X.Wm + (key_r(key) >> 5)], ~(1u << (key_r(key) & 31)));
 }
-template <typename IX>
-__device__ void unlink_col(const Sim<IX> &X, int si, int key)
+template <class S>
+__device__ void unlink_col(const S &X, int si, int key)
 {
+    using IX = typename S::ix;
     const int p = SLOTF(X, cp, si), q = SLOTF(X, cn, si);
     IX *h = &X.colHead[key_d(key) * X.n + key_c(key)];
     if (p >= 0) SLOTF(X, cn, p) = (IX)q; else *h = (IX)q;
@@ -691,9 +710,10 @@ __device__ void unlink_col(const Sim<IX> &X, int si, int key)
 
 // Link a slot into its row list and its column list (both head loads first:
 // the two lists are independent).
-template <typename IX>
-__device__ __forceinline__ void push_both(const Sim<IX> &X, int si, int key)
+template <class S>
+__device__ __forceinline__ void push_both(const S &X, int si, int key)
 {
+    using IX = typename S::ix;
     IX *hr = &X.rowHead[key_d(key) * X.m + key_r(key)];
     IX *hc = &X.colHead[key_d(key) * X.n + key_c(key)];
     const int oldR = *hr, oldC = *hc;
@@ -708,9 +728,10 @@ __device__ __forceinline__ void push_both(const Sim<IX> &X, int si, int key)
 }
 // Lanes in `pend` link their slots, one lane at a time (two of them may
 // share a list).
-template <typename IX>
-__device__ __forceinline__ void push_lanes(const Sim<IX> &X, unsigned pend, int si, int key)
+template <class S>
+__device__ __forceinline__ void push_lanes(const S &X, unsigned pend, int si, int key)
 {
+    using IX = typename S::ix;
     const int lane = threadIdx.x & 31;
     for (; pend; pend &= pend - 1) {
         if (lane == __ffs(pend) - 1) push_both(X, si, key);
@@ -739,9 +760,10 @@ __device__ int bit_scan(const uint32_t *b, int limit, int pos, int delta, int ma
 }
 
 // Lowest move id held in slots [0, hi) and its slot (warp-cooperative).
-template <typename IX>
-__device__ int lowest_slot(const Sim<IX> &X, int hi)
+template <class S>
+__device__ int lowest_slot(const S &X, int hi)
 {
+    using IX = typename S::ix;
     const int lane = threadIdx.x & 31;
     int best = INTMAX, bs = -1;
     for (int i = lane; i < hi; i += 32) {
@@ -798,10 +820,11 @@ __device__ void warp_sort64(long long *a, int n)
 
 // Allocate `cnt` slots (warp-cooperative); lane `rank` < cnt gets a slot.
 // freeTop / ovfUsed / hi are warp-uniform.
-template <typename IX>
-__device__ __forceinline__ int alloc_slot(const Sim<IX> &X, int rank, int cnt, int &freeTop, int &ovfFreeTop,
+template <class S>
+__device__ __forceinline__ int alloc_slot(const S &X, int rank, int cnt, int &freeTop, int &ovfFreeTop,
                                           int &ovfUsed, int &hi, int kmax, int *err)
 {
+    using IX = typename S::ix;
     int si = -1;
     const int fromStack = min(cnt, freeTop);
     const int fromOvf = min(cnt - fromStack, ovfFreeTop);
@@ -814,17 +837,20 @@ __device__ __forceinline__ int alloc_slot(const Sim<IX> &X, int rank, int cnt, i
     // the overflow area holds kmax + 1 slots, and slot indices must stay
     // representable in the link type: beyond either, no slot (nothing is
     // written) and the run ends with an error
-    const int lastOk = min(X.C + kmax, sizeof(IX) == 2 ? 32767 : 0x7fffffff);
+    // (narrow: the shared capacity; beyond it the instance is handed to the
+    // wide simulation)
+    const int lastOk = S::wide ? min(X.C + kmax, sizeof(IX) == 2 ? 32767 : 0x7fffffff) : X.C - 1;
     if (si > lastOk) si = -1;
-    if (ovfUsed > kmax || X.C + ovfUsed > lastOk + 1) *err = RR_ERR_INTERNAL;
-    hi = X.C + ovfUsed;            // every slot ever used lies below
+    if (ovfUsed > kmax || X.C + ovfUsed > lastOk + 1) *err = S::wide ? RR_ERR_INTERNAL : RR_SIM_RETRY;
+    hi = S::wide ? X.C + ovfUsed : X.C;   // every slot ever used lies below
     return si;
 }
 
 // A newly ready move: fill its slot (the caller links it into the lists).
-template <typename IX>
-__device__ __forceinline__ int fill_slot(const Sim<IX> &X, int si, int id, int4 r)
+template <class S>
+__device__ __forceinline__ int fill_slot(const S &X, int si, int id, int4 r)
 {
+    using IX = typename S::ix;
     int rr, cc, d, rem, len;
     move_pos(r.x, r.y, 0, &rr, &cc, &d, &rem, &len);
     const int key = key_of(rr, cc, d);
@@ -860,9 +886,10 @@ __device__ __forceinline__ void prefetch_succ(const JobWS &ws, int4 s4, int nsuc
 // Turn the members back into statics (warp-cooperative). Members share one
 // line, so their perpendicular lists are distinct and are pushed in
 // parallel; the shared line list gets the members as one spliced chain.
-template <typename IX>
-__device__ void dissolve(const Sim<IX> &X, int nm, bool rowLine)
+template <class S>
+__device__ void dissolve(const S &X, int nm, bool rowLine)
 {
+    using IX = typename S::ix;
     const int lane = threadIdx.x & 31;
     if (nm <= 0) return;
     const int k0 = SLOTF(X, key, X.Msl[0]) & ~KEY_MEM;
@@ -948,7 +975,7 @@ __global__ void k_classify(rr_instance *inst, int count, int nclass, int max_sid
     }
 }
 
-template <typename IX>
+template <typename IX, bool WIDE>
 __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int count, const int *classList,
                                          const int *classCount, int slotCap, int lineCap)
 {
@@ -960,16 +987,29 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
     }
     if (q >= count) return;
     rr_instance *I = &inst[q];
-    if (!live(I)) return;
+    if (WIDE ? I->status != RR_SIM_RETRY : !live(I)) return;
     JobWS &ws = wsv[q];
     const int k = (int)I->n_moves;
     const int m = I->m, n = I->n;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     if (k == 0) { if (lane == 0) { I->n_ops = 0; I->n_members = 0; } return; }
+    if (WIDE) {
+        // the narrow pass consumed in-degrees before giving up: recount them
+        // from the successor lists, then start over
+        for (int b = lane; b < k; b += 32) ws.indeg[b] = 0;
+        __syncwarp();
+        for (int b = lane; b < k; b += 32) {
+            const int lo = ws.pairOff[b], cnt = ws.succCnt[b];
+            for (int e = 0; e < cnt; ++e) atomicAdd(&ws.indeg[ws.succ[lo + e] & SUCC_ID], 1);
+        }
+        __syncwarp();
+        __threadfence_block();
+        if (lane == 0) I->status = RR_OK;
+    }
 
     // shared-memory layout (mirrored by the launcher's size computation)
-    Sim<IX> X;
+    Sim<IX, WIDE> X;
     X.C = slotCap; X.m = m; X.n = n; X.Wm = (m + 31) >> 5; X.Wn = (n + 31) >> 5;
     const int lbuf = 2 * (lineCap + 2);
     X.Kb = (long long *)smem_i4;
@@ -1037,7 +1077,9 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
     int overflow = 0;
     int Ls = lowest_slot(X, hi);
     int L = Ls >= 0 ? SLOTF(X, id, Ls) : -1;
-    if (L != 0) err = RR_ERR_INTERNAL;
+    if (err) {
+        // out of slots already (narrow pass): handed to the wide pass
+    } else if (L != 0) err = RR_ERR_INTERNAL;
     else {
         if (lane == 0) { const int kk = SLOTF(X, key, Ls); unlink_row(X, Ls, kk); unlink_col(X, Ls, kk); }
         __syncwarp();
@@ -1231,6 +1273,20 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
             // successor entries of the finished moves, in rounds of SBUF
             const int off = warp_incl_scan(nsu) - nsu;
             const int total = __shfl_sync(FULL, off + nsu, 31);
+            // free the finished moves first (their successors may take the slots)' slots (shared-memory ones are recycled)
+            if (fin) {
+                const int id = SLOTF(X, id, si);
+                if (X.map[id & (MAPN - 1)] == si) X.map[id & (MAPN - 1)] = -1;
+                SLOTF(X, key, si) = 0;
+                SLOTF(X, id, si) = INTMAX;
+            }
+            const bool recyc = fin && si < X.C, recycO = fin && si >= X.C;
+            const unsigned fb = __ballot_sync(FULL, recyc), fo = __ballot_sync(FULL, recycO);
+            if (recyc) X.freeStk[freeTop + __popc(fb & lt)] = (int16_t)si;
+            if (recycO) X.ovfFree[ovfFreeTop + __popc(fo & lt)] = si;
+            freeTop += __popc(fb);
+            ovfFreeTop += __popc(fo);
+            __syncwarp();
             for (int base = 0; base < total; base += SBUF) {
                 if (fin) {
                     for (int e = max(0, base - off); e < nsu && off + e < base + SBUF; ++e)
@@ -1261,20 +1317,6 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
                     __syncwarp();
                 }
             }
-            // free the finished moves' slots (shared-memory ones are recycled)
-            if (fin) {
-                const int id = SLOTF(X, id, si);
-                if (X.map[id & (MAPN - 1)] == si) X.map[id & (MAPN - 1)] = -1;
-                SLOTF(X, key, si) = 0;
-                SLOTF(X, id, si) = INTMAX;
-            }
-            const bool recyc = fin && si < X.C, recycO = fin && si >= X.C;
-            const unsigned fb = __ballot_sync(FULL, recyc), fo = __ballot_sync(FULL, recycO);
-            if (recyc) X.freeStk[freeTop + __popc(fb & lt)] = (int16_t)si;
-            if (recycO) X.ovfFree[ovfFreeTop + __popc(fo & lt)] = si;
-            freeTop += __popc(fb);
-            ovfFreeTop += __popc(fo);
-            __syncwarp();
         }
         for (int u = lane; u < nkeep; u += 32) { X.Mid[u] = (int)(X.Kb[u] >> 32); X.Msl[u] = (int)(X.Kb[u] & 0xffffffff); }
         nm = nkeep;
@@ -1326,15 +1368,27 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
 } // namespace rrk
 
 namespace rrk {
-// 16-bit slot links (sides up to 256) and 32-bit ones.
+// 16-bit slot links (sides up to 256) and 32-bit ones; narrow (shared-memory
+// slots only) and wide (overflow slots in global memory, for the instances
+// the narrow pass handed over).
 __global__ void k_sim16(rr_instance *inst, JobWS *wsv, int count, const int *classList, const int *classCount,
                         int slotCap, int lineCap)
 {
-    sim_body<int16_t>(inst, wsv, count, classList, classCount, slotCap, lineCap);
+    sim_body<int16_t, false>(inst, wsv, count, classList, classCount, slotCap, lineCap);
 }
 __global__ void k_sim32(rr_instance *inst, JobWS *wsv, int count, const int *classList, const int *classCount,
                         int slotCap, int lineCap)
 {
-    sim_body<int32_t>(inst, wsv, count, classList, classCount, slotCap, lineCap);
+    sim_body<int32_t, false>(inst, wsv, count, classList, classCount, slotCap, lineCap);
+}
+__global__ void k_sim16w(rr_instance *inst, JobWS *wsv, int count, const int *classList, const int *classCount,
+                         int slotCap, int lineCap)
+{
+    sim_body<int16_t, true>(inst, wsv, count, classList, classCount, slotCap, lineCap);
+}
+__global__ void k_sim32w(rr_instance *inst, JobWS *wsv, int count, const int *classList, const int *classCount,
+                         int slotCap, int lineCap)
+{
+    sim_body<int32_t, true>(inst, wsv, count, classList, classCount, slotCap, lineCap);
 }
 }  // namespace rrk

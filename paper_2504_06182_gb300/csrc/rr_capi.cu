@@ -34,6 +34,8 @@ __global__ void k_gather(const rr_instance *, const int *, rr_instance *);
 __global__ void k_scatter(rr_instance *, const int *, const rr_instance *, int);
 __global__ void k_sim16(rr_instance *, JobWS *, int, const int *, const int *, int, int);
 __global__ void k_sim32(rr_instance *, JobWS *, int, const int *, const int *, int, int);
+__global__ void k_sim16w(rr_instance *, JobWS *, int, const int *, const int *, int, int);
+__global__ void k_sim32w(rr_instance *, JobWS *, int, const int *, const int *, int, int);
 }  // namespace rrk
 
 using namespace rrk;
@@ -44,7 +46,7 @@ static_assert(sizeof(rr_instance) == 128, "rr_instance layout is part of the ABI
 static constexpr int SMALL_CALL = 8;
 
 // Kernels launched with more than the default 48 KB of dynamic shared memory.
-enum { SM_GSORT, SM_GSWEEP_H, SM_GSWEEP_V, SM_SIM16, SM_SIM32, SM_NKERNEL };
+enum { SM_GSORT, SM_GSWEEP_H, SM_GSWEEP_V, SM_SIM16, SM_SIM32, SM_SIM16W, SM_SIM32W, SM_NKERNEL };
 
 struct rr_ctx {
     int device;
@@ -136,7 +138,8 @@ static int smem_limits(int dev, int *out)
         int optin = 0;
         cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         const void *fn[SM_NKERNEL] = {(const void *)k_gsort, (const void *)k_gsweep_h, (const void *)k_gsweep_v,
-                                      (const void *)k_sim16, (const void *)k_sim32};
+                                      (const void *)k_sim16, (const void *)k_sim32, (const void *)k_sim16w,
+                                      (const void *)k_sim32w};
         for (int i = 0; e == cudaSuccess && i < SM_NKERNEL; ++i) {
             cudaFuncAttributes fa;
             e = cudaFuncGetAttributes(&fa, fn[i]);
@@ -397,12 +400,20 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, 
         // ends with an internal error instead of wrapping an index
         const bool narrow = lineCap <= 256;
         const size_t simSmem = sim_smem_bytes(slotCap, lineCap, narrow ? 2 : 4);
-        if (simSmem > (size_t)ctx->smemLimit[narrow ? SM_SIM16 : SM_SIM32])
+        if (simSmem > (size_t)std::min(ctx->smemLimit[narrow ? SM_SIM16 : SM_SIM32],
+                                       ctx->smemLimit[narrow ? SM_SIM16W : SM_SIM32W]))
             return fail(ctx, RR_ERR_ARG, "simulation shared memory %zu too large", simSmem);
         const int *list = one ? nullptr : ctx->d_classList + (size_t)c * count;
         const int *cnt = one ? nullptr : ctx->d_classCount + c;
-        if (narrow) k_sim16<<<count, 32, simSmem, cs>>>(d_inst, ws, count, list, cnt, slotCap, lineCap);
-        else k_sim32<<<count, 32, simSmem, cs>>>(d_inst, ws, count, list, cnt, slotCap, lineCap);
+        // the narrow pass, then the wide one for the instances it handed over
+        // (its blocks of other instances return at once)
+        if (narrow) {
+            k_sim16<<<count, 32, simSmem, cs>>>(d_inst, ws, count, list, cnt, slotCap, lineCap);
+            k_sim16w<<<count, 32, simSmem, cs>>>(d_inst, ws, count, list, cnt, slotCap, lineCap);
+        } else {
+            k_sim32<<<count, 32, simSmem, cs>>>(d_inst, ws, count, list, cnt, slotCap, lineCap);
+            k_sim32w<<<count, 32, simSmem, cs>>>(d_inst, ws, count, list, cnt, slotCap, lineCap);
+        }
         if (!one) {
             CUDA_TRY(cudaEventRecord(ctx->evJoin[c], cs));
             CUDA_TRY(cudaStreamWaitEvent(s, ctx->evJoin[c], 0));
@@ -410,7 +421,7 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, 
     }
     mark(ctx, s, nullptr);
     CUDA_TRY(cudaGetLastError());
-    ctx->nlaunch += (one ? 14 : 15) + nclass;
+    ctx->nlaunch += (one ? 14 : 15) + 2 * nclass;
     return RR_OK;
 }
 

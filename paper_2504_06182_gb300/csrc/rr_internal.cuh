@@ -112,6 +112,12 @@ __host__ __device__ inline size_t sim_smem_bytes(int slotCap, int lineCap, int i
            64;
 }
 
+// Status of an instance between the two simulation passes: the narrow pass
+// (shared-memory slots only) ran out of slots and the wide pass redoes it.
+// The wide pass always follows in the same launch sequence, so callers never
+// see it.
+constexpr int32_t RR_SIM_RETRY = 100;
+
 // Successor entries carry this flag when the successor has a single
 // predecessor: it becomes ready as soon as that predecessor finishes.
 constexpr int32_t SUCC_SINGLE = 1 << 30;

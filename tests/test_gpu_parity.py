@@ -186,6 +186,28 @@ def test_batch_general_move_lists(planner):
         assert (ops.cpu().numpy() == rops).all() and (mem.cpu().numpy() == rmem).all()
 
 
+def test_batch_beyond_shared_slots(planner):
+    """A move list with far more ready moves than the simulation's shared
+    slots (512 one-step moves all ready at once on a 32 x 32 grid, then the
+    way back): the narrow pass hands the instance to the wide one, whose
+    batches equal the oracle's; and a red-rec plan in the same context stays
+    exact afterwards."""
+    from tests.checks import replay_moves
+    m = n = 32
+    g = np.zeros((m, n), np.uint8)
+    g[:, 0::2] = 1
+    out = [(r, c, r, c + 1) for r in range(m) for c in range(0, n, 2)]
+    back = [(r, c + 1, r, c) for r in range(m) for c in range(0, n, 2)]
+    moves = np.array(out + back, dtype=np.int32)
+    replay_moves(g, None, [tuple(x) for x in moves])          # a legal sequence
+    rops, rmem = oracle.batch(moves, m, n)
+    ops, mem = planner.batch(torch.from_numpy(moves).cuda(), m, n)
+    assert (ops.cpu().numpy() == rops).all() and (mem.cpu().numpy() == rmem).all()
+    from paper_2504_06182_gb300 import RR_U8
+    inst = gridgen.square_instance(5, 1, 48, 0.6)
+    check_instance(planner, inst.grid, inst.rect, RR_U8)
+
+
 def test_batched_entry_point_mixed_sizes(planner):
     """Mixed 32..256 bit-packed grids through one rr_plan_batched call with
     batching, each compared with the oracle."""
