@@ -58,6 +58,21 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seed(seed, rank):
+    """Each rank plans its own grids (weak scaling, no data-path collective)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(value, device, world):
+    """The slowest rank's time: the job's time."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -403,7 +418,7 @@ def run_ours(args, rank, world, local):
     import paper_2504_06182_gb300 as rr
     from paper_2504_06182_gb300.planner import Planner, pack_instances, unpack_instances
 
-    insts = gridgen.mixed_instances(args.seed + 1000 * rank, args.count)
+    insts = gridgen.mixed_instances(rank_seed(args.seed, rank), args.count)
     # CPU oracle baseline on host cores before any GPU work (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -512,11 +527,7 @@ def run_ours(args, rank, world, local):
         torch.distributed.barrier()
     clk = clocks.stop() if rank == 0 else None
     rr.rr_set_tracing(P.ctx, False)
-    elapsed_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(sum(times), dev, world)
 
     # the same step replayed from a captured CUDA graph (RR_GRAPH)
     gflags = rr.RR_WITH_BATCH | rr.RR_GRAPH
@@ -557,11 +568,7 @@ def run_ours(args, rank, world, local):
         b.record(stream)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e_total = float(sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_ms), dev, world)
 
     if rank != 0:
         if world > 1:
