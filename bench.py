@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=1000,
                     help="requests of the served high-load run (0: skip the served runs)")
     ap.add_argument("--served-load", type=float, default=0.8, help="arrival rate as a fraction of saturation")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch configuration (for profiling fixed launches)")
     ap.add_argument("--configs", action="store_true",
                     help="instead of the bench line: one line per single-grid config (32^2, 256^2, 1024^2), "
                          "plain GPU latency and the single-thread oracle, median over seeds")
@@ -492,7 +494,8 @@ def run_ours(args, rank, world, local):
 
     # launch configuration picked by the library's autotuner on this workload
     # (before the warm-up; not timed)
-    tuned_nclass, tuned_shift, tuned_pipe = rr.rr_autotune(P.ctx, d_inst, count, max_side, rr.RR_WITH_BATCH, stream)
+    tuned_nclass, tuned_shift, tuned_pipe = (4, 0, 1) if args.no_autotune else \
+        rr.rr_autotune(P.ctx, d_inst, count, max_side, rr.RR_WITH_BATCH, stream)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -619,7 +622,8 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grids_per_gpu": count, "layout": "bits32", "seed": args.seed,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world}",
-                   "autotuned": {"size_classes": tuned_nclass, "block_budget_scale": 2.0 ** tuned_shift,
+                   "autotuned": None if args.no_autotune else {"size_classes": tuned_nclass,
+                                                               "block_budget_scale": 2.0 ** tuned_shift,
                                  "largest_first": ["off", "1/4", "1/16, 1/4", "1/16, 1/8, 1/4, 1/2"][tuned_pipe]}},
         "e2e": {"value": count * world * args.steps / (e2e_total * 1e-3), "unit": "grids/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
