@@ -583,9 +583,9 @@ constexpr int INTMAX = 0x7fffffff;
 template <typename IX> struct SlotSoA {
     int32_t *key;     // row | col << 10 | dir << 20 | KEY_LIVE [| KEY_MEM]; 0 when free
     int32_t *id;      // move id, INT_MAX when free
-    int32_t *g0, *g1; // src_row | src_col << 16, dst_row | dst_col << 16
     int16_t *t;       // elementary steps done (paths are shorter than 2 048 steps)
     int16_t *legEnd;  // t at the end of the current straight leg
+    int16_t *dstRow;  // destination row: where the last (vertical) leg ends
     IX *rp, *rn, *cp, *cn;        // static-list links (slot indices, -1)
     // a move's successors are read from its record when it finishes: only
     // the leader and the members ever finish
@@ -638,16 +638,6 @@ __device__ __forceinline__ int key_of(int r, int c, int d) { return r | (c << 10
 __device__ __forceinline__ int key_r(int k) { return k & 1023; }
 __device__ __forceinline__ int key_c(int k) { return (k >> 10) & 1023; }
 __device__ __forceinline__ int key_d(int k) { return (k >> 20) & 3; }
-
-// Position, direction and remaining straight leg after t steps of a move.
-__device__ __forceinline__ void move_pos(int g0, int g1, int t, int *r, int *c, int *d, int *rem, int *len)
-{
-    const int sr = g0 & 0xffff, sc = g0 >> 16, dr = g1 & 0xffff, dc = g1 >> 16;
-    const int hl = iabs(dc - sc);
-    *len = hl + iabs(dr - sr);
-    if (t < hl) { *d = dc > sc ? 3 : 2; *r = sr; *c = sc + (dc > sc ? t : -t); *rem = hl - t; }
-    else { const int v = t - hl; *d = dr > sr ? 1 : 0; *r = sr + (dr > sr ? v : -v); *c = dc; *rem = *len - t; }
-}
 
 __device__ __forceinline__ int warp_min(int v)
 {
@@ -851,15 +841,16 @@ template <class S>
 __device__ __forceinline__ int fill_slot(const S &X, int si, int id, int4 r)
 {
     using IX = typename S::ix;
-    int rr, cc, d, rem, len;
-    move_pos(r.x, r.y, 0, &rr, &cc, &d, &rem, &len);
-    const int key = key_of(rr, cc, d);
+    // the first leg: along the source row if the move changes column, else
+    // along the column (an L-path runs row first, then column)
+    const int sr = r.x & 0xffff, sc = r.x >> 16, dr = r.y & 0xffff, dc = r.y >> 16;
+    const int d = dc != sc ? (dc > sc ? 3 : 2) : (dr > sr ? 1 : 0);
+    const int key = key_of(sr, sc, d);
     SLOTF(X, key, si) = key;
     SLOTF(X, id, si) = id;
-    SLOTF(X, g0, si) = r.x;
-    SLOTF(X, g1, si) = r.y;
     SLOTF(X, t, si) = 0;
-    SLOTF(X, legEnd, si) = (int16_t)rem;
+    SLOTF(X, legEnd, si) = (int16_t)(dc != sc ? iabs(dc - sc) : iabs(dr - sr));
+    SLOTF(X, dstRow, si) = (int16_t)dr;
     X.map[id & (MAPN - 1)] = si;
     return key;
 }
@@ -1016,8 +1007,6 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
     int32_t *p32 = (int32_t *)(X.Kb + lbuf);
     X.sm.key = p32; p32 += slotCap;
     X.sm.id = p32; p32 += slotCap;
-    X.sm.g0 = p32; p32 += slotCap;
-    X.sm.g1 = p32; p32 += slotCap;
     X.map = p32; p32 += MAPN;
     X.Mid = p32; p32 += lineCap + 2;
     X.Msl = p32; p32 += lineCap + 2;
@@ -1034,17 +1023,19 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
     int16_t *p16 = (int16_t *)pix;
     X.sm.t = p16; p16 += slotCap;
     X.sm.legEnd = p16; p16 += slotCap;
+    X.sm.dstRow = p16; p16 += slotCap;
     X.freeStk = p16;
     X.ovfFree = ws.ovfFree;
     {   // overflow slots (global), same structure
         char *g = (char *)ws.slotOvf;
         const size_t K1 = (size_t)k + 1;
-        int32_t **f[4] = {&X.gm.key, &X.gm.id, &X.gm.g0, &X.gm.g1};
-        for (int u = 0; u < 4; ++u) { *f[u] = (int32_t *)g; g += 4 * K1; }
+        X.gm.key = (int32_t *)g;           g += 4 * K1;
+        X.gm.id = (int32_t *)g;            g += 4 * K1;
         IX **fl[4] = {&X.gm.rp, &X.gm.rn, &X.gm.cp, &X.gm.cn};
         for (int u = 0; u < 4; ++u) { *fl[u] = (IX *)g; g += sizeof(IX) * K1; }
         X.gm.t = (int16_t *)g;             g += 2 * K1;
-        X.gm.legEnd = (int16_t *)g;
+        X.gm.legEnd = (int16_t *)g;        g += 2 * K1;
+        X.gm.dstRow = (int16_t *)g;
     }
     for (int i = lane; i < slotCap; i += 32) { X.sm.key[i] = 0; X.sm.id[i] = INTMAX; X.freeStk[i] = (int16_t)(slotCap - 1 - i); }
     for (int i = lane; i < MAPN; i += 32) X.map[i] = -1;
@@ -1093,8 +1084,10 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
 
     while (!err && L < k) {
         if (++guard > guard_max) { err = RR_ERR_TIMEOUT; break; }
-        int lr, lc, d, remL, lenL;
-        move_pos(SLOTF(X, g0, Ls), SLOTF(X, g1, Ls), SLOTF(X, t, Ls), &lr, &lc, &d, &remL, &lenL);
+        // the leader's position and direction are in its key (kept current)
+        const int kL = SLOTF(X, key, Ls);
+        const int lr = key_r(kL), lc = key_c(kL), d = key_d(kL);
+        const int remL = SLOTF(X, legEnd, Ls) - SLOTF(X, t, Ls);
         const int sgn = (d == 1 || d == 3) ? 1 : -1;
         // members still on the leader's line in the leader's direction?
         if (nm > 0 && !(dm == d && (rowLine ? lineIdx == lr : lineIdx == lc))) { dissolve(X, nm, rowLine); nm = 0; }
@@ -1244,11 +1237,22 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
             int4 fs4 = make_int4(0, 0, 0, 0);
             if (act) {
                 si = u == 0 ? Ls : X.Msl[u - 1];
+                // kseg steps along the current leg (no batch move's leg ends
+                // before the segment does), then finish or turn at its end
+                const int key = SLOTF(X, key, si);
                 const int t = SLOTF(X, t, si) + kseg;
-                int r_, c_, d_, rem, len;
-                move_pos(SLOTF(X, g0, si), SLOTF(X, g1, si), t, &r_, &c_, &d_, &rem, &len);
+                const int le = SLOTF(X, legEnd, si);
+                int d_ = key_d(key);
+                const int r_ = key_r(key) + (d_ == 1 ? kseg : d_ == 0 ? -kseg : 0);
+                const int c_ = key_c(key) + (d_ == 3 ? kseg : d_ == 2 ? -kseg : 0);
+                int rem = le - t;
                 SLOTF(X, t, si) = (int16_t)t;
-                fin = t >= len;
+                if (rem == 0) {
+                    const int dr = SLOTF(X, dstRow, si);
+                    fin = r_ == dr;
+                    d_ = dr > r_ ? 1 : 0;
+                    rem = iabs(dr - r_);
+                }
                 if (fin) {
                     const int id = SLOTF(X, id, si);
                     const int4 own = ws.rec[2 * id];
@@ -1259,7 +1263,7 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
                     turn = u > 0 && d_ != d;
                     newKey = key_of(r_, c_, d_) | (u > 0 && !turn ? KEY_MEM : 0);
                     SLOTF(X, key, si) = newKey;
-                    SLOTF(X, legEnd, si) = (int16_t)(t + rem);
+                    if (t + rem != le) SLOTF(X, legEnd, si) = (int16_t)(t + rem);
                 }
             }
             if (u0 == 0 && __shfl_sync(FULL, (int)fin, 0)) leaderDone = 1;

@@ -106,9 +106,9 @@ __host__ __device__ inline size_t sim_smem_bytes(int slotCap, int lineCap, int i
 {
     const size_t S = (size_t)slotCap, L = (size_t)lineCap;
     return 8 * 2 * (L + 2) +                                            // Kb
-           4 * (4 * S + MAPN + 2 * (L + 2) + SBUF + 4 * ((L + 31) / 32)) +  // key id g0 g1, map, Mid Msl, sbuf, bits
+           4 * (2 * S + MAPN + 2 * (L + 2) + SBUF + 4 * ((L + 31) / 32)) +  // key id, map, Mid Msl, sbuf, bits
            (size_t)ix * (4 * S + 8 * L) +                                // rp rn cp cn, row and column heads
-           2 * 3 * S +                                                   // t, legEnd, free stack
+           2 * 4 * S +                                                   // t, legEnd, dstRow, free stack
            64;
 }
 
