@@ -639,6 +639,13 @@ def run_ours(args, rank, world, local):
         "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_tot.items(), key=lambda kv: -kv[1])},
         "totals_per_step": {"moves": int(tot_moves), "ops": int(tot_ops), "steps": int(tot_mem),
                             "feasible": int(feasible), "grids": count},
+        # control operations of one reconfiguration cycle (§V): displacement
+        # operations N_nu = elementary steps, transfer operations N_alpha = one
+        # extraction and one implantation per move, batched displacement
+        # sequences NB_nu = batches (the paper defines no batching of transfers)
+        "control_ops_per_feasible_grid": {
+            "N_nu": tot_mem / max(1, feasible), "N_alpha": 2 * tot_moves / max(1, feasible),
+            "NB_nu": tot_ops / max(1, feasible), "N_nu_per_NB_nu": tot_mem / max(1, tot_ops)},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
