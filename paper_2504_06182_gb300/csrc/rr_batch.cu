@@ -1195,7 +1195,7 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
         int kseg = remL;
         int remM = INTMAX;
         for (int u = lane; u < nm; u += 32) { const int si = X.Msl[u]; remM = min(remM, SLOTF(X, legEnd, si) - SLOTF(X, t, si)); }
-        kseg = min(kseg, warp_min(remM));
+        kseg = min(kseg, __reduce_min_sync(FULL, remM));   // one warp reduction
         if (kseg > 1) {   // a static move of direction d the leader's line reaches
             const int hit = d >= 2 ? bit_scan(X.colBits + (d - 2) * X.Wn, n, lc, sgn, kseg - 1)
                                    : bit_scan(X.rowBits + d * X.Wm, m, lr, sgn, kseg - 1);
@@ -1275,9 +1275,11 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
             // members whose leg ended become statics
             push_lanes(X, __ballot_sync(FULL, turn), si, newKey);
             // successor entries of the finished moves, in rounds of SBUF
+            if (!__any_sync(FULL, fin)) continue;     // nothing finished in this chunk
             const int off = warp_incl_scan(nsu) - nsu;
             const int total = __shfl_sync(FULL, off + nsu, 31);
-            // free the finished moves first (their successors may take the slots)' slots (shared-memory ones are recycled)
+            // free the finished moves' slots first (their successors may take
+            // them; shared-memory slots are recycled)
             if (fin) {
                 const int id = SLOTF(X, id, si);
                 if (X.map[id & (MAPN - 1)] == si) X.map[id & (MAPN - 1)] = -1;
