@@ -624,7 +624,7 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"dp{world}",
                    "autotuned": None if args.no_autotune else {"size_classes": tuned_nclass,
                                                                "block_budget_scale": 2.0 ** tuned_shift,
-                                 "largest_first": ["off", "1/4", "1/16, 1/4", "1/16, 1/8, 1/4, 1/2"][tuned_pipe]}},
+                                 "largest_first": ["off", "1/4", "1/16, 1/4", "1/16, 1/8, 1/4, 1/2", "1/64, 1/16, 1/4"][tuned_pipe]}},
         "e2e": {"value": count * world * args.steps / (e2e_total * 1e-3), "unit": "grids/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,

@@ -130,9 +130,9 @@ int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, i
  * timed with CUDA events on `stream` (best of two each): first under nine
  * configurations (2, 4 or 8 simulation size classes, times per-grid block
  * budgets of the planning and graph kernels scaled by 1/2, 1 or 2), then,
- * with the best of those, under four pipeline splits (see below): 0 none,
+ * with the best of those, under five pipeline splits (see below): 0 none,
  * 1 the largest quarter first, 2 the largest 1/16 then up to 1/4, 3 groups
- * ending at 1/16, 1/8, 1/4 and 1/2. The fastest is kept in the context for
+ * ending at 1/16, 1/8, 1/4 and 1/2, 4 groups ending at 1/64, 1/16 and 1/4. The fastest is kept in the context for
  * later rr_plan_batched calls (a captured RR_GRAPH graph is dropped) and
  * written to *nclass, *shift (log2 of the budget scale) and *pipe (the
  * split) when those are not NULL. Every

@@ -197,7 +197,7 @@ def rr_stage_times(ctx, cap: int = 32):
 
 def rr_autotune(ctx, d_inst, count, max_side, flags=RR_WITH_BATCH, stream=None):
     """Picks and keeps the fastest launch configuration for these instances.
-    Returns (size classes, log2 block-budget scale, pipeline split 0..3)."""
+    Returns (size classes, log2 block-budget scale, pipeline split 0..4)."""
     nc, sh, pd = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
     st = load().rr_autotune(ctx, _addr(d_inst), int(count), int(max_side), int(flags), _stream(stream),
                             ctypes.byref(nc), ctypes.byref(sh), ctypes.byref(pd))

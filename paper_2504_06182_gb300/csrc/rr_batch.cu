@@ -639,6 +639,17 @@ __device__ __forceinline__ int key_r(int k) { return k & 1023; }
 __device__ __forceinline__ int key_c(int k) { return (k >> 10) & 1023; }
 __device__ __forceinline__ int key_d(int k) { return (k >> 20) & 3; }
 
+// a % b for 0 <= a <= 32 < 2^24 and b >= 1: a float quotient, corrected
+// by one either way (exact: the error of the product is far below 1)
+__device__ __forceinline__ int small_mod(int a, int b)
+{
+    const int q = __float2int_rz((float)a * __frcp_rn((float)b));
+    int r = a - q * b;
+    if (r < 0) r += b;
+    if (r >= b) r -= b;
+    return r;
+}
+
 __device__ __forceinline__ int warp_min(int v)
 {
 #pragma unroll
@@ -1211,8 +1222,8 @@ __device__ __forceinline__ void sim_body(rr_instance *inst, JobWS *wsv, int coun
             if (ns == 1) {
                 for (int i = lane; i < kseg; i += 32) mem[nmem + i] = L;
             } else {
-                int u = lane % ns;
-                const int step = 32 % ns;
+                int u = small_mod(lane, ns);
+                const int step = small_mod(32, ns);
                 for (int64_t i = lane; i < addm; i += 32) {
                     mem[nmem + i] = u == 0 ? L : X.Mid[u - 1];
                     u += step;

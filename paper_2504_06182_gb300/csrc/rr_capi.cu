@@ -485,12 +485,14 @@ extern "C" int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, in
 static constexpr int PIPE_MIN = 256;
 // Pipeline splits: the leading groups end at these fractions of the grids
 // (ordered by side, largest first); the rest forms the last group.
-static constexpr int PIPE_SPLITS = 4;
-static const int PIPE_FRAC16[PIPE_SPLITS][rr_ctx::MAXLEAD] = {
+// (in 64ths of the call's grids)
+static constexpr int PIPE_SPLITS = 5;
+static const int PIPE_FRAC64[PIPE_SPLITS][rr_ctx::MAXLEAD] = {
     {0, 0, 0, 0},          // none
-    {4, 0, 0, 0},          // the largest quarter, then the rest
-    {1, 4, 0, 0},          // 1/16, 1/4
-    {1, 2, 4, 8},          // 1/16, 1/8, 1/4, 1/2
+    {16, 0, 0, 0},         // the largest quarter, then the rest
+    {4, 16, 0, 0},         // 1/16, 1/4
+    {4, 8, 16, 32},        // 1/16, 1/8, 1/4, 1/2
+    {1, 4, 16, 0},         // 1/64, 1/16, 1/4
 };
 
 // The whole sequence of one rr_plan_batched call on `stream`.
@@ -508,7 +510,7 @@ static int launch_sequence(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
 {
     CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
     const bool plan = !(flags & RR_BATCH_ONLY), batch = (flags & (RR_WITH_BATCH | RR_BATCH_ONLY)) != 0;
-    const int *frac = PIPE_FRAC16[ctx->pipe > 0 && ctx->pipe < PIPE_SPLITS ? ctx->pipe : 0];
+    const int *frac = PIPE_FRAC64[ctx->pipe > 0 && ctx->pipe < PIPE_SPLITS ? ctx->pipe : 0];
     if (!batch || frac[0] == 0 || count < PIPE_MIN) {
         int st = plan ? launch_plan(ctx, d_inst, ctx->d_ws, count, max_side, stream) : RR_OK;
         if (st == RR_OK && batch)
@@ -523,7 +525,7 @@ static int launch_sequence(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
     int st = RR_OK, lo = 0, ng = 0;
     cudaEvent_t prevSim = nullptr;
     for (int g = 0; g < rr_ctx::MAXLEAD && frac[g] && st == RR_OK; ++g) {
-        const int hi = std::max(lo + 1, (int)((int64_t)count * frac[g] / 16));
+        const int hi = std::max(lo + 1, (int)((int64_t)count * frac[g] / 64));
         if (hi >= count) break;
         cudaStream_t gs = ctx->leadStream[g];
         CUDA_TRY(cudaStreamWaitEvent(gs, ctx->evStart, 0));
