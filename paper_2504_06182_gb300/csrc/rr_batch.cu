@@ -650,13 +650,6 @@ __device__ __forceinline__ int small_mod(int a, int b)
     return r;
 }
 
-__device__ __forceinline__ int warp_min(int v)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(FULL, v, o));
-    return v;
-}
-
 template <class S>
 __device__ __forceinline__ void bits_set(const S &X, int d, int r, int c)
 {
