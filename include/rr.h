@@ -239,7 +239,9 @@ int rr_stage_times(rr_ctx *ctx, float *ms, const char **names, int cap);
  * RR_ERR_ARG for a null argument. */
 int rr_launch_count(rr_ctx *ctx, int64_t *launches);
 
-/* Last error text of this context (static storage, never NULL). */
+/* Last error text of this context; with ctx NULL, of the calling thread's
+ * last call that had no context (e.g. a failed rr_ctx_create). Never NULL;
+ * valid until the next call on the same context or thread. */
 const char *rr_last_error(rr_ctx *ctx);
 
 #ifdef __cplusplus

@@ -101,7 +101,8 @@ static void mark(rr_ctx *ctx, cudaStream_t s, const char *name)
     ++ctx->nmarks;
 }
 
-static char g_err[256] = "";
+// error text of calls without a context (per thread: calls may come from several)
+static thread_local char g_err[256] = "";
 
 static int fail(rr_ctx *ctx, int code, const char *fmt, ...)
 {
