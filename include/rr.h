@@ -150,6 +150,13 @@ int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, i
 int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
                 cudaStream_t stream, int32_t *nclass, int32_t *shift, int32_t *pipe);
 
+/* Sets the launch configuration of later rr_plan_batched calls directly (as
+ * rr_autotune leaves it): nclass in [1, 8] simulation size classes, block
+ * budgets scaled by 2^shift (shift in [-3, 3]), pipeline split pipe in
+ * [0, 4] (as above). Drops a captured RR_GRAPH graph. Results do not depend
+ * on the configuration. The defaults are nclass 4, shift 0, pipe 1. */
+int rr_set_config(rr_ctx *ctx, int nclass, int shift, int pipe);
+
 /* ------------------------------------------------------------------ serving
  * Continuous batching of planning requests (red-rec + batching per request):
  * a request is admitted as soon as its grid and its move list (room for

@@ -65,7 +65,7 @@ class rr_serve_result(ctypes.Structure):
 
 
 EXPORTS = ("rr_ctx_create", "rr_ctx_destroy", "rr_plan", "rr_batch", "rr_plan_batched", "rr_set_tracing",
-           "rr_stage_times", "rr_launch_count", "rr_autotune", "rr_last_error", "rr_plan_noalloc", "rr_serve_open", "rr_serve_submit",
+           "rr_stage_times", "rr_launch_count", "rr_autotune", "rr_set_config", "rr_last_error", "rr_plan_noalloc", "rr_serve_open", "rr_serve_submit",
            "rr_serve_poll", "rr_serve_release", "rr_serve_close")
 RR_NOALLOC_MAX_SIDE = 256
 
@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH):
     L.rr_autotune.argtypes = [P, P, I32, I32, I32, P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(ctypes.c_int32)]
     L.rr_autotune.restype = I32
+    L.rr_set_config.argtypes = [P, I32, I32, I32]
+    L.rr_set_config.restype = I32
     L.rr_plan_noalloc.argtypes = [P, I32, I32, I32, rr_rect, P, I64, ctypes.POINTER(I64), P]
     L.rr_plan_noalloc.restype = I32
     L.rr_serve_open.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(rr_serve_config)]
@@ -204,6 +206,15 @@ def rr_autotune(ctx, d_inst, count, max_side, flags=RR_WITH_BATCH, stream=None):
     if st != RR_OK:
         raise RRError(st, rr_last_error(ctx))
     return int(nc.value), int(sh.value), int(pd.value)
+
+
+def rr_set_config(ctx, nclass, shift, pipe) -> int:
+    """Sets the batched launch configuration (size classes, log2 block-budget
+    scale, pipeline split)."""
+    st = load().rr_set_config(ctx, int(nclass), int(shift), int(pipe))
+    if st != RR_OK:
+        raise RRError(st, rr_last_error(ctx))
+    return st
 
 
 def rr_launch_count(ctx) -> int:

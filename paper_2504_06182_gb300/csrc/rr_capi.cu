@@ -676,6 +676,17 @@ extern "C" int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
     return st;
 }
 
+extern "C" int rr_set_config(rr_ctx *ctx, int nclass, int shift, int pipe)
+{
+    if (!ctx || nclass < 1 || nclass > rr_ctx::MAXCLASS || shift < -3 || shift > 3 || pipe < 0 || pipe >= PIPE_SPLITS)
+        return fail(ctx, RR_ERR_ARG, "rr_set_config: bad argument (nclass=%d shift=%d pipe=%d)", nclass, shift, pipe);
+    ctx->nclass = nclass;
+    ctx->shift = shift;
+    ctx->pipe = pipe;
+    drop_graph(ctx);
+    return RR_OK;
+}
+
 // Library-internal: size a context's descriptor table for `count` instances
 // up front (the server does this before any wave so that no call allocates).
 int rr_internal_reserve(rr_ctx *ctx, int count) { return ensure_ws(ctx, count); }

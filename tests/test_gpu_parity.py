@@ -331,6 +331,96 @@ def test_autotune_then_batched(planner):
             assert (mem[: r.n_members].cpu().numpy() == rmem).all() and r.n_members == len(rmem)
 
 
+def test_batched_pipelined_every_config(planner):
+    """360 grids (at least 256, so the call is pipelined by size) under every
+    pipeline split and several class counts: every status, move list, batch
+    list and member list equals the oracle's, including grids given too
+    little room for their moves (RR_ERR_CAPACITY with the required count) and
+    infeasible ones; then the same moves through a pipelined RR_BATCH_ONLY
+    call."""
+    import paper_2504_06182_gb300 as rr
+    from paper_2504_06182_gb300.planner import pack_instances, unpack_instances
+    insts = gridgen.mixed_instances(13, 360, sides=(32, 48, 64, 96, 128), p_lo=0.55, p_hi=0.7)
+    refs = [oracle.plan(i.grid, i.rect) for i in insts]
+    short = {g for g in range(len(insts)) if g % 17 == 5 and len(refs[g].moves) > 1}
+    assert short and any(r.status == 1 for r in refs)
+    bats = {}
+    entries, outs = [], []
+    for g, (inst, ref) in enumerate(zip(insts, refs)):
+        s = inst.grid.shape[0]
+        k = max(len(ref.moves), 1)
+        steps = int((np.abs(ref.moves[:, 0] - ref.moves[:, 2]) + np.abs(ref.moves[:, 1] - ref.moves[:, 3])).sum()) \
+            if len(ref.moves) else 0
+        cap = 1 if g in short else k
+        mv = torch.empty((k, 4), dtype=torch.int32, device="cuda")
+        ops = torch.empty((max(steps, 1), 3), dtype=torch.int32, device="cuda")
+        mem = torch.empty((max(steps, 1),), dtype=torch.int32, device="cuda")
+        entries.append(dict(grid=to_device(inst.grid, rr.RR_BITS32), layout=rr.RR_BITS32, m=s, n=s, rect=inst.rect,
+                            moves=mv, cap_moves=cap, ops=ops, cap_ops=max(steps, 1), members=mem,
+                            cap_members=max(steps, 1)))
+        outs.append((mv, ops, mem))
+        if ref.status == 0 and g not in short:
+            bats[g] = oracle.batch(ref.moves, s, s)
+
+    def check(res, batch_only=False):
+        for g, (r, ref) in enumerate(zip(res, refs)):
+            mv, ops, mem = outs[g]
+            if batch_only:
+                if ref.status != 0 or g in short:
+                    continue
+            elif g in short:
+                assert r.status == rr.RR_ERR_CAPACITY and r.n_moves == len(ref.moves), (g, r.status)
+                continue
+            else:
+                assert r.status == (rr.RR_OK if ref.status == 0 else rr.RR_INFEASIBLE), (g, r.status)
+                assert r.n_moves == len(ref.moves)
+                if ref.status != 0:
+                    continue
+                assert (mv[: r.n_moves].cpu().numpy() == ref.moves).all(), g
+            rops, rmem = bats[g]
+            assert r.n_ops == len(rops) and r.n_members == len(rmem), g
+            assert (ops[: r.n_ops].cpu().numpy() == rops).all(), g
+            assert (mem[: r.n_members].cpu().numpy() == rmem).all(), g
+
+    dev = pack_instances(entries)
+    for nclass, pipe in [(4, 0), (4, 1), (2, 2), (8, 3), (4, 4), (1, 4)]:
+        rr.rr_set_config(planner.ctx, nclass, 0, pipe)
+        for t in outs:
+            for x in t:
+                x.zero_()
+        assert rr.rr_plan_batched(planner.ctx, dev, len(entries), 128, rr.RR_WITH_BATCH) == rr.RR_OK
+        torch.cuda.synchronize()
+        check(unpack_instances(dev, len(entries)))
+    # the moves as input: descriptors of the feasible grids that had room
+    keep = [g for g in range(len(insts)) if refs[g].status == 0 and g not in short]
+    assert len(keep) >= 256
+    ent2 = []
+    for g in keep:
+        e = dict(entries[g])
+        e["cap_moves"] = len(refs[g].moves)
+        ent2.append(e)
+    raw = pack_instances(ent2)
+    host = unpack_instances(raw, len(ent2))
+    for x, g in zip(host, keep):
+        x.n_moves = len(refs[g].moves)
+        x.status = rr.RR_OK
+    arr = (rr.rr_instance * len(ent2))(*host)
+    dev2 = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).cuda()
+    rr.rr_set_config(planner.ctx, 4, 0, 2)
+    for g in keep:
+        outs[g][1].zero_()
+        outs[g][2].zero_()
+    assert rr.rr_plan_batched(planner.ctx, dev2, len(ent2), 128, rr.RR_BATCH_ONLY) == rr.RR_OK
+    torch.cuda.synchronize()
+    res2 = unpack_instances(dev2, len(ent2))
+    for x, g in zip(res2, keep):
+        rops, rmem = bats[g]
+        _, ops, mem = outs[g]
+        assert x.status == rr.RR_OK and x.n_ops == len(rops) and x.n_members == len(rmem), g
+        assert (ops[: x.n_ops].cpu().numpy() == rops).all() and (mem[: x.n_members].cpu().numpy() == rmem).all(), g
+    rr.rr_set_config(planner.ctx, 4, 0, 1)
+
+
 def test_grid_1024_bit_layout(planner):
     """Full-size 1024 x 1024 grid with a centred 720 x 720 target: the whole
     move list against the oracle, and the batches against the oracle (all of
