@@ -12,15 +12,18 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_served_results_equal_alone():
+@pytest.mark.parametrize("max_wave", [5, 12])
+def test_served_results_equal_alone(max_wave):
+    """Waves of at most 5 run the simulation as one launch; waves of 12 fork
+    it into size classes."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_2504_06182_gb300 as rr
     from paper_2504_06182_gb300.planner import Planner, device_view
 
     insts = gridgen.mixed_instances(77, 40, sides=tuple(range(32, 257, 32)), p_lo=0.55, p_hi=0.7)
-    srv = rr.rr_serve_open(max_side=256, slots=12, streams=3, max_wave=5, flags=rr.RR_WITH_BATCH,
-                           arena_bytes=1 << 30, heap_bytes=1 << 30)
+    srv = rr.rr_serve_open(max_side=256, slots=max(12, 2 * max_wave), streams=3, max_wave=max_wave,
+                           flags=rr.RR_WITH_BATCH, arena_bytes=1 << 30, heap_bytes=1 << 30)
     P = Planner(arena_bytes=1 << 30)
     try:
         tickets = []
@@ -50,7 +53,7 @@ def test_served_results_equal_alone():
                 assert torch.equal(device_view(res.d_members, (res.n_members,)), mem_ref)
             overlapped += res.t_admit_us > res.t_submit_us
             assert rr.rr_serve_release(srv, t) == rr.RR_OK
-        # with 12 slots and 40 requests submitted at once, later ones waited for slots
+        # with fewer slots than the 40 requests submitted at once, later ones waited
         assert overlapped > 0
         # unknown ticket and oversize grids are refused
         assert rr.rr_serve_poll(srv, 10 ** 9)[0] == rr.RR_ERR_ARG
