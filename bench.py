@@ -613,8 +613,9 @@ def run_ours(args, rank, world, local):
                     "frac": ach / peak_gbs, "traffic": int(ratio * byt) if ratio else None,
                     "peak_source": "measured" if peaks else "fallback",
                     "alg_bytes_per_launch": int(byt), "avg_ms": avg_ms,
-                    "launch": "one step's simulation: the four size-class launches, timed together "
-                              "from fork to join on the launching stream" if dom == "k_sim" else "one launch"}
+                    "launch": "one step's simulation: every simulation launch of the step (pipeline groups "
+                              "and size classes), timed from the first one's start to the join after the last"
+                              if dom == "k_sim" else "one launch"}
     value = count * world * args.steps / (elapsed_ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "grids/s", "n_gpus": world, "steps": args.steps,
