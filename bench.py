@@ -55,8 +55,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch configuration (for profiling fixed launches)")
     ap.add_argument("--configs", action="store_true",
-                    help="instead of the bench line: one line per single-grid config (32^2, 256^2, 1024^2), "
-                         "plain GPU latency and the single-thread oracle, median over seeds")
+                    help="instead of the bench line: one line per single-grid config (32^2, 256^2, 1024^2) "
+                         "and one for 1024-trap chains: plain GPU latency and the single-thread oracle")
     return ap.parse_args()
 
 
@@ -727,6 +727,7 @@ def run_configs(args):
         cpu[side] = {"kind": "oracle", "cores": 1, "plan_us": float(np.median(plan_us)),
                      "plan_batch_us": float(np.median(both_us)) if both_us else None,
                      "sample": sample or f"seeds 0..{seeds[-1]}, one grid at a time"}
+    cpu_chain = oracle_chain_us()
     import torch
     import paper_2504_06182_gb300 as rr
     from paper_2504_06182_gb300.planner import Planner
@@ -763,7 +764,64 @@ def run_configs(args):
                         "path": "one rr_plan (and rr_batch) call per grid, grid resident on the device, synchronised"},
                 "cpu_baseline": cpu[side], "seed0_outputs": outs, "data": "synthetic"}
         print(json.dumps(line), flush=True)
+    run_chains(rr, P, cpu_chain)
     P.close()
+
+
+CHAIN_TRAPS = 1024
+CHAIN_COUNT = 16384
+
+
+def oracle_chain_us():
+    """Single-thread oracle latency of one 1024-trap chain (median of 200)."""
+    import oracle
+    inst = gridgen.chain_instance(0, 0, CHAIN_TRAPS)
+    return median_us(lambda: oracle.plan(inst.grid, inst.rect), 200)
+
+
+def run_chains(rr, P, cpu_us):
+    """The paper's 1D workload: chains of 1024 traps with a centred target of
+    512 (eta = 0.5), fill 0.6. One chain per rr_plan call, and 16384 chains
+    per rr_plan_batched call (planning only: the exact 1D solve)."""
+    import torch
+    from paper_2504_06182_gb300.planner import pack_instances, unpack_instances
+    one = gridgen.chain_instance(0, 0, CHAIN_TRAPS)
+    g1 = torch.from_numpy(np.ascontiguousarray(one.grid)).cuda()
+
+    def plan1():
+        r = P.plan(g1, one.rect, layout=rr.RR_U8, n=1, cap=2 * CHAIN_TRAPS)
+        torch.cuda.synchronize()
+        return r
+    plan1()
+    plain_us = median_us(plan1, 200)
+    insts = [gridgen.chain_instance(1, g, CHAIN_TRAPS) for g in range(CHAIN_COUNT)]
+    grids = torch.from_numpy(np.ascontiguousarray(np.concatenate([i.grid.ravel() for i in insts]))).cuda()
+    moves = torch.empty((CHAIN_COUNT * 2 * CHAIN_TRAPS, 4), dtype=torch.int32, device="cuda")
+    entries = [dict(grid=grids[g * CHAIN_TRAPS:(g + 1) * CHAIN_TRAPS], layout=rr.RR_U8, m=CHAIN_TRAPS, n=1,
+                    rect=insts[g].rect, moves=moves[g * 2 * CHAIN_TRAPS:], cap_moves=2 * CHAIN_TRAPS)
+               for g in range(CHAIN_COUNT)]
+    dev = pack_instances(entries)
+    stream = torch.cuda.current_stream()
+    times = []
+    for it in range(6):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rr.rr_plan_batched(P.ctx, dev, CHAIN_COUNT, CHAIN_TRAPS, 0, stream)
+        b.record(stream)
+        b.synchronize()
+        if it:
+            times.append(a.elapsed_time(b))
+    res = unpack_instances(dev, CHAIN_COUNT)
+    bad = sum(x.status not in (rr.RR_OK, rr.RR_INFEASIBLE) for x in res)
+    line = {"config": f"chains of {CHAIN_TRAPS} traps, centred target of {CHAIN_TRAPS // 2} (eta 0.5), p = 0.6",
+            "metric": "exact 1D solve: per-chain latency and batched chains/s", "unit": "us, chains/s",
+            "gpu": {"plan_us": plain_us,
+                    "batched_chains_per_s": CHAIN_COUNT / (float(np.median(times)) * 1e-3),
+                    "batched": f"{CHAIN_COUNT} chains per rr_plan_batched call, median of 5", "failed": int(bad)},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "plan_us": cpu_us, "sample": "one chain, median of 200"},
+            "paper_context": {"cpu_serial_us": 22, "hw": "AMD Threadripper 2950X"},
+            "data": "synthetic (Bernoulli loading stands in for the paper's exact 0.6 n_t atoms)"}
+    print(json.dumps(line), flush=True)
 
 
 def main():

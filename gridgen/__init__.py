@@ -115,6 +115,14 @@ def paper_instance(seed: int, g: int, n_tx: int, p: float = 0.6) -> Instance:
     return Instance(grid, centred_rect(m, n_tx, n_tx, n_tx), seed, g, p)
 
 
+def chain_instance(seed: int, g: int, n_t: int, p: float = 0.6) -> Instance:
+    """The paper's 1D workload: a chain of n_t traps (an n_t x 1 grid), fill p,
+    a centred target of n_t / 2 traps (eta = 0.5). The paper loads exactly
+    0.6 n_t atoms at random; Bernoulli(p) loading stands in for that."""
+    grid = grid_u8(seed, g, n_t, 1, threshold(p))
+    return Instance(grid, centred_rect(n_t, 1, n_t // 2, 1), seed, g, p)
+
+
 def mixed_draw(seed: int, g: int, sides, p_lo: float, p_hi: float):
     """Per-grid (side, p) for mixed-size workloads: side uniform over `sides`,
     p uniform in [p_lo, p_hi], both from outputs 2**32 and 2**32 + 1 of grid

@@ -123,6 +123,42 @@ def test_paper_geometry(planner, n_tx):
     assert seen == {0, 1}
 
 
+def test_chains(planner):
+    """The paper's 1D workload: chains of 16 to 1024 traps (n x 1 grids) with
+    a centred target of half the traps; plans and batches equal the
+    oracle's, one chain per call and many per batched call."""
+    import paper_2504_06182_gb300 as rr
+    from paper_2504_06182_gb300.planner import pack_instances, unpack_instances
+    insts = [gridgen.chain_instance(43, g, n_t) for n_t in (16, 64, 256, 1024) for g in range(6)]
+    refs = [oracle.plan(i.grid, i.rect) for i in insts]
+    assert {r.status for r in refs} == {0, 1}
+    for inst in insts[::5]:
+        check_instance(planner, inst.grid, inst.rect, rr.RR_U8)
+    entries, outs = [], []
+    for inst, ref in zip(insts, refs):
+        m = inst.grid.shape[0]
+        k = max(len(ref.moves), 1)
+        steps = max(1, int(np.abs(ref.moves[:, 0] - ref.moves[:, 2]).sum()) if len(ref.moves) else 1)
+        mv = torch.empty((k, 4), dtype=torch.int32, device="cuda")
+        ops = torch.empty((steps, 3), dtype=torch.int32, device="cuda")
+        mem = torch.empty((steps,), dtype=torch.int32, device="cuda")
+        entries.append(dict(grid=to_device(inst.grid, rr.RR_BITS32), layout=rr.RR_BITS32, m=m, n=1, rect=inst.rect,
+                            moves=mv, cap_moves=k, ops=ops, cap_ops=steps, members=mem, cap_members=steps))
+        outs.append((mv, ops, mem))
+    dev = pack_instances(entries)
+    assert rr.rr_plan_batched(planner.ctx, dev, len(entries), 1024, rr.RR_WITH_BATCH) == rr.RR_OK
+    torch.cuda.synchronize()
+    for inst, ref, r, (mv, ops, mem) in zip(insts, refs, unpack_instances(dev, len(entries)), outs):
+        assert r.status == (rr.RR_OK if ref.status == 0 else rr.RR_INFEASIBLE)
+        assert r.n_moves == len(ref.moves)
+        if ref.status != 0:
+            continue
+        assert (mv[: r.n_moves].cpu().numpy() == ref.moves).all()
+        rops, rmem = oracle.batch(ref.moves, inst.grid.shape[0], 1)
+        assert (ops[: r.n_ops].cpu().numpy() == rops).all() and r.n_ops == len(rops)
+        assert (mem[: r.n_members].cpu().numpy() == rmem).all() and r.n_members == len(rmem)
+
+
 def test_edge_cases(planner):
     from paper_2504_06182_gb300 import RR_BITS32, RR_U8
     cases = []
