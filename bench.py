@@ -189,7 +189,7 @@ def measured_traffic_ratio(kernel):
 
 # ------------------------------------------------------------- paper geometry
 
-PAPER_NTX = (32, 64, 128, 256)
+PAPER_NTX = (32, 48, 64, 96, 128, 192, 256)
 PAPER_CONTEXT = {"n_tx": 32, "cpu_us": 106, "cpu_hw": "AMD Threadripper 2950X, serial",
                  "gpu_us": 197, "gpu_hw": "Nvidia Quadro RTX 4000, one kernel"}
 
