@@ -1,8 +1,8 @@
 """ctypes wrapper of the sequential CPU oracle (rr_oracle.c).
 
-TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
-CPU-baseline leg are the only users of this package. The CUDA library and its
-Python binding never import it.
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baselines (its cpu_baseline legs and its reference arm) are the only users of
+this package. The CUDA library and its Python binding never import it.
 """
 from __future__ import annotations
 

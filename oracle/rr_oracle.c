@@ -5,8 +5,9 @@
  * set of Sec. IV), arXiv 2504.06182.
  *
  * TEST INFRASTRUCTURE ONLY: the plain, slow statement of what the planner
- * computes. The tests, the smoke check and the benchmark's CPU-baseline leg
- * are its only users; it shares no code with the CUDA library.
+ * computes. The tests, the smoke check and the benchmark's CPU baselines
+ * (its cpu_baseline legs and its reference arm) are its only users; it
+ * shares no code with the CUDA library.
  *
  * Every choice the paper leaves open is fixed here, once:
  *  - Exact 1D with a contiguous target interval (Sec. III.A, "Assignment"):
