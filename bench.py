@@ -4,7 +4,7 @@
 Workload (one step): 4096 independent square grids, side uniform over
 {32, 48, ..., 256}, fill p uniform in [0.5, 0.7], centred target of side
 floor(0.7 * side), bit-packed uint32 rows; the whole batch is planned
-(Alg. 1) and batched (Alg. 2) by one rr_plan_batched(RR_WITH_BATCH) call.
+(Alg. 1) and batched (Alg. 4) by one rr_plan_batched(RR_WITH_BATCH) call.
 Inputs are seeded synthetic grids (gridgen), resident in HBM before timing.
 
 `--impl reference` times the CPU oracle instead (bounded samples of the same

@@ -4,7 +4,7 @@
  * Method: Afiouni et al., "Efficient algorithms to solve atom reconfiguration
  * problems III" (arXiv 2504.06182): the improved red-rec algorithm (Alg. 1,
  * Sec. III.C, executed in the column order of the parallel variant of Sec.
- * III.D) and the batching routine (Alg. 2 with the local constraint set of
+ * III.D) and the batching routine (Alg. 4 with the local constraint set of
  * Sec. IV). All arithmetic is integer.
  *
  * Memory: every buffer argument named d_* is caller-owned DEVICE memory; the
@@ -51,7 +51,7 @@ typedef struct { int32_t r0, c0, r1, c1; } rr_rect;
  * column dst_col from src_row to dst_row. */
 typedef struct { int32_t src_row, src_col, dst_row, dst_col; } rr_move;
 
-/* One batch of Alg. 2: members[first .. first+count) are the ids (indices into
+/* One batch of Alg. 4: members[first .. first+count) are the ids (indices into
  * the move list) of the moves whose tokens advance one elementary step in
  * direction dir: 0 = row-1, 1 = row+1, 2 = column-1, 3 = column+1. */
 typedef struct { int32_t dir, first, count; } rr_op;
@@ -74,7 +74,7 @@ int rr_ctx_destroy(rr_ctx *ctx);
 int rr_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect,
             rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream);
 
-/* Batch a move list (Alg. 2 + Sec. IV): dependencies = every earlier move
+/* Batch a move list (Alg. 4 + Sec. IV): dependencies = every earlier move
  * whose path shares a vertex; ready moves are visited in ascending id and a
  * move's next step joins the batch iff it has the first member's direction and
  * its token shares a row or a column with every member's token. d_moves must

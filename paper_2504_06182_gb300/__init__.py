@@ -1,5 +1,5 @@
 """GB300 red-rec planner and batching routine (arXiv 2504.06182, Alg. 1 and
-Alg. 2) -- Python binding of the C ABI in include/rr.h.
+Alg. 4) -- Python binding of the C ABI in include/rr.h.
 
 The functions below carry the C names and only marshal arguments: every step
 of the planning and batching path runs in the CUDA library librr.so. PyTorch

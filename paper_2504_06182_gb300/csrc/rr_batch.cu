@@ -1,4 +1,4 @@
-// rr_batch.cu -- the batching routine (arXiv 2504.06182, Alg. 2 with the
+// rr_batch.cu -- the batching routine (arXiv 2504.06182, Alg. 4 with the
 // local constraint set of Sec. IV) on the GPU.
 //
 // Gamma (Sec. IV, "Input to the batching routine"): move b depends on every
@@ -8,7 +8,7 @@
 // list of paths through it in id order, and from it the de-duplicated
 // successor lists and in-degrees.
 //
-// Alg. 2 itself runs as an event-driven simulation, one warp per instance.
+// Alg. 4 itself runs as an event-driven simulation, one warp per instance.
 // The lowest-id unfinished move is always ready (nothing earlier is
 // unfinished), so it is always the first member ("leader") of the batch. With
 // the leader's token at (r, c) moving in direction d, the other members are

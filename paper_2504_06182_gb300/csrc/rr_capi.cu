@@ -1,5 +1,5 @@
 // rr_capi.cu -- the C ABI (include/rr.h): context, workspace arena and the
-// launch sequences of the planner (Alg. 1) and the batching routine (Alg. 2).
+// launch sequences of the planner (Alg. 1) and the batching routine (Alg. 4).
 #include <cstdio>
 #include <cstring>
 #include <cstdarg>

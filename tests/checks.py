@@ -1,7 +1,7 @@
 """Independent checkers used by the tests: they restate the paper's validity
 conditions directly (Sec. II.B-C: an unobstructed move needs every vertex of
 its path other than the source free of tokens; a valid path system fills T;
-Alg. 2: a batch holds at most one next edge per path, pairwise disjoint; Sec.
+Alg. 4: a batch holds at most one next edge per path, pairwise disjoint; Sec.
 IV: every pair of tokens in a batch moves in the same direction and shares a
 row or a column). They share no code with the oracle or the CUDA library.
 """
@@ -97,7 +97,7 @@ def replay_ops(grid, moves, ops, members):
 
 
 def batch_bruteforce(moves):
-    """Alg. 2 with Gamma taken literally: a path is ready iff no earlier
+    """Alg. 4 with Gamma taken literally: a path is ready iff no earlier
     unfinished path shares a vertex with it; ready paths are visited in id
     order and a next step joins iff it has the first member's direction and
     its token shares a row or a column with every member's token. Quadratic;

@@ -195,7 +195,7 @@ def test_capacity_and_arguments(planner):
 
 
 def test_batch_general_move_lists(planner):
-    """Alg. 2 on arbitrary unobstructed move sequences (not only red-rec output)."""
+    """Alg. 4 on arbitrary unobstructed move sequences (not only red-rec output)."""
     from tests.checks import replay_moves
     rng = np.random.default_rng(99)
     for trial in range(60):

@@ -1,7 +1,7 @@
-"""Pins of the oracle's batching routine (Alg. 2 with the local constraints of
+"""Pins of the oracle's batching routine (Alg. 4 with the local constraints of
 Sec. IV), CPU only.
 
-P7 batches <= elementary steps (Alg. 2 deletes at least one edge per
+P7 batches <= elementary steps (Alg. 4 deletes at least one edge per
 iteration); P8 conservation (every elementary step appears in exactly one
 batch) and replay equivalence; P9 the per-batch constraints; and the oracle's
 dependency bookkeeping against Gamma taken literally (every earlier path that
@@ -42,7 +42,7 @@ def test_batching_matches_literal_gamma():
 
 
 def test_batching_random_move_lists():
-    """Alg. 2 is defined for any valid ordered path system, not only red-rec
+    """Alg. 4 is defined for any valid ordered path system, not only red-rec
     output: random unobstructed move sequences on random grids."""
     for trial in range(150):
         m, n = int(RNG.integers(2, 8)), int(RNG.integers(2, 8))

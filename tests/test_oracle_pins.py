@@ -3,7 +3,7 @@
 P1 replay legality (Sec. II.B-C), P2 optimality of the 1D solves against a
 library assignment solver and exhaustive search (Sec. III.A), P4 the 2n-chain
 closed form (Sec. III.A, Complexity), P5 special cases, P6 feasibility
-(Sec. III.C), P7 iteration bounds (Sec. III.C Complexity, Alg. 2), pairing
+(Sec. III.C), P7 iteration bounds (Sec. III.C Complexity, Alg. 4), pairing
 choices against exhaustive pair enumeration (Sec. III.C), and the geometry
 invariants of the generated path system (Sec. III.A, III.C).
 """
