@@ -45,6 +45,8 @@ def lib():
         L.rro_split.restype = i32
         L.rro_plan.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, i64, P]
         L.rro_plan.restype = i32
+        L.rro_bird.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, i64, P]
+        L.rro_bird.restype = i32
         L.rro_batch.argtypes = [P, i64, i32, i32, P, i64, P, i64, P, P]
         L.rro_batch.restype = i32
         L.rro_batch_prefix.argtypes = [P, i64, i32, i32, i64, P, i64, P, i64, P, P]
@@ -104,6 +106,31 @@ def plan(grid: np.ndarray, rect, with_trace: bool = False) -> Plan:
         raise RuntimeError(f"oracle rro_plan failed with status {st}")
     return Plan(st, moves[: nm.value].copy(), sigma,
                 events[: ne.value].copy() if with_trace else None)
+
+
+def bird(grid: np.ndarray, rect, with_trace: bool = False) -> Plan:
+    """The bird planner (Alg. 2, Sec. III.E). With with_trace, events holds
+    one row per receiver: (column, tokens from above the band, tokens from
+    below it); sigma is not filled."""
+    grid = np.ascontiguousarray(grid, dtype=np.uint8)
+    m, n = grid.shape
+    r0, c0, r1, c1 = (int(v) for v in rect)
+    nm = ctypes.c_int64(0)
+    nu = ctypes.c_int64(0)
+    cap = 0
+    cap_u = n + 1 if with_trace else 0
+    units = np.zeros((max(cap_u, 1), 3), dtype=np.int32)
+    while True:
+        moves = np.zeros((max(cap, 1), 4), dtype=np.int32)
+        st = lib().rro_bird(_ptr(grid), m, n, r0, c0, r1, c1, _ptr(moves), cap, ctypes.byref(nm),
+                            _ptr(units) if with_trace else None, cap_u, ctypes.byref(nu))
+        if st == ERR_CAPACITY:
+            cap = nm.value
+            continue
+        break
+    if st not in (OK, INFEASIBLE):
+        raise RuntimeError(f"oracle rro_bird failed with status {st}")
+    return Plan(st, moves[: nm.value].copy(), None, units[: nu.value].copy() if with_trace else None)
 
 
 def batch(moves: np.ndarray, m: int, n: int, max_ops: int | None = None, cap: int = 0):

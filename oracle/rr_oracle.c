@@ -1,8 +1,9 @@
 /*
  * rr_oracle.c -- sequential CPU oracle for the improved red-rec planner
  * (Alg. 1, Sec. III.C, in the column order of the parallel variant of
- * Sec. III.D) and for the batching routine (Alg. 2 with the local constraint
- * set of Sec. IV), arXiv 2504.06182.
+ * Sec. III.D), the bird planner (Alg. 2, Sec. III.E) and the batching
+ * routine (Alg. 4 with the local constraint set of Sec. IV), arXiv
+ * 2504.06182.
  *
  * TEST INFRASTRUCTURE ONLY: the plain, slow statement of what the planner
  * computes. The tests, the smoke check and the benchmark's CPU baselines
@@ -40,9 +41,20 @@
  *    left at equal distance), below it nearest column first (left before
  *    right), so nearer tokens get the deeper targets and clear the shared
  *    corridor first.
+ *  - bird (Sec. III.E): the column phase is red-rec's; then the unsolved
+ *    columns are taken left to right. The generalised 1D instance of column
+ *    j holds all of j's atoms at their rows and every atom in a reservoir row
+ *    of every other column, projected along its diagonal onto j (row - d
+ *    above the band, row + d below it, d the column distance). The optimal
+ *    window over the sorted tokens (smallest start on ties) fixes how many
+ *    tokens each vertex gives; a vertex holding several gives its nearest
+ *    columns' tokens, left before right at equal distance. Tokens are then
+ *    matched in order, with the same order on one vertex as red-rec's
+ *    projected tokens (nearer tokens get the targets farther along their
+ *    direction), and emitted as one unit.
  *  - Dependencies Gamma (Sec. IV, "Input to the batching routine"): path b
  *    depends on every earlier path whose vertex set meets its own.
- *  - Batching (Alg. 2 + Sec. IV "Constrained batching"): ready paths are
+ *  - Batching (Alg. 4 + Sec. IV "Constrained batching"): ready paths are
  *    visited in ascending id; a path's next step joins the batch iff it moves
  *    in the first member's direction and its current cell shares a row or a
  *    column with the current cell of every member already in the batch.
@@ -407,6 +419,155 @@ done:
     if (marked) for (int c = 0; c < n; ++c) free(marked[c].v);
     free(K); free(sigma); free(atoms); free(pool); free(marked);
     free(unit); free(src); free(scratch); free(out.v);
+    return st;
+}
+
+/* -------------------------------------------------------- the bird planner */
+
+/* One token of the generalised 1D instance of a receiver column (Sec. III.E).
+ * pos is the token's vertex on the receiver's column: its own row for the
+ * receiver's own atoms; for an atom in a reservoir row v of another column at
+ * column distance d, v - d above the band and v + d below it, so that
+ * |pos - t| is the Manhattan distance to band trap t of the receiver. */
+typedef struct { int32_t pos, row, col; } btok_t;
+
+/* Order of the tokens of receiver g_rcv: by vertex; on one vertex above the
+ * band the farther column first (right before left at equal distance), below
+ * it the nearer column first (left before right). The nearest tokens of a
+ * vertex are thus the last ones above the band and the first ones below it. */
+static int cmp_btok(const void *pa, const void *pb)
+{
+    const btok_t *a = (const btok_t *)pa, *b = (const btok_t *)pb;
+    if (a->pos != b->pos) return a->pos < b->pos ? -1 : 1;
+    int da = abs(a->col - g_rcv), db = abs(b->col - g_rcv);
+    int ra = a->col > g_rcv, rb = b->col > g_rcv;
+    if (a->pos < g_r0) {
+        if (da != db) return da > db ? -1 : 1;
+        if (ra != rb) return ra ? -1 : 1;
+    } else {
+        if (da != db) return da < db ? -1 : 1;
+        if (ra != rb) return ra ? 1 : -1;
+    }
+    g_tie_bug = 1;                     /* same cell twice */
+    return 0;
+}
+
+/* Executes one unit on the occupancy grid: every source is vacated, then
+ * every destination filled (an isolated path leaves its atom in place). */
+static void apply_unit(uint8_t *cur, int n, const mv_t *u, int cnt)
+{
+    for (int k = 0; k < cnt; ++k) cur[(size_t)u[k].sr * n + u[k].sc] = 0;
+    for (int k = 0; k < cnt; ++k) cur[(size_t)u[k].dr * n + u[k].dc] = 1;
+}
+
+int rro_bird(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
+             int32_t *moves, int64_t cap, int64_t *n_moves,
+             int32_t *units, int64_t cap_units, int64_t *n_units)
+{
+    if (!grid || !n_moves || m < 1 || n < 1 || r0 < 0 || r0 >= r1 || r1 > m ||
+        c0 < 0 || c0 >= c1 || c1 > n || cap < 0 || (cap > 0 && !moves))
+        return E_ARG;
+    const int h = r1 - r0, R = m - h;
+    int st = OK;
+    int64_t nu = 0, tot = 0;
+    mvvec_t out = {0};
+    uint8_t *cur = (uint8_t *)malloc((size_t)m * n);
+    uint8_t *recv = (uint8_t *)calloc((size_t)n, 1);
+    int32_t *rows = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    mv_t *unit = (mv_t *)malloc(sizeof(mv_t) * (size_t)(m + 1));
+    btok_t *T = (btok_t *)malloc(sizeof(btok_t) * ((size_t)m * n + 1));
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * ((size_t)m * n + 1));
+    uint8_t *take = (uint8_t *)malloc((size_t)m * n + 1);
+    if (!cur || !recv || !rows || !unit || !T || !pos || !take) { st = E_NOMEM; goto done; }
+    memcpy(cur, grid, (size_t)m * n);
+    for (size_t v = 0; v < (size_t)m * n; ++v) cur[v] = grid[v] != 0;
+
+    /* Columns of non-negative surplus are solved first with the exact 1D
+     * algorithm, exactly as in red-rec's column phase (including the
+     * virtual solve of columns outside the target columns). */
+    for (int c = 0; c < n; ++c) {
+        int K = 0, cnt = 0;
+        for (int r = 0; r < m; ++r) if (cur[(size_t)r * n + c]) rows[K++] = r;
+        if (c >= c0 && c < c1) {
+            tot += K - h;
+            if (K < h) { recv[c] = 1; continue; }
+            int w = rro_window(rows, K, r0, h);
+            if (w < 0) { st = E_BUG; goto done; }
+            for (int k = 0; k < h; ++k) unit[cnt++] = (mv_t){rows[w + k], c, r0 + k, c};
+        } else if (K >= R) {
+            const int nbot = m - r1;
+            for (int k = 0; k < r0; ++k) unit[cnt++] = (mv_t){rows[k], c, k, c};
+            for (int k = 0; k < nbot; ++k) unit[cnt++] = (mv_t){rows[K - nbot + k], c, r1 + k, c};
+            tot += R;
+        } else {
+            for (int k = 0; k < K; ++k) tot += rows[k] < r0 || rows[k] >= r1;
+        }
+        apply_unit(cur, n, unit, cnt);
+        if ((st = emit_unit(&out, unit, cnt)) != OK) goto done;
+    }
+    if (tot < 0) { st = INFEASIBLE; out.n = 0; goto done; }
+
+    /* Main loop of the bird algorithm: the leftmost unsolved column is filled
+     * from every token of the grid at once, through its generalised 1D
+     * instance; then the next one. */
+    for (int j = c0; j < c1; ++j) {
+        if (!recv[j]) continue;
+        int nt = 0;
+        for (int c = 0; c < n; ++c)
+            for (int r = 0; r < m; ++r) {
+                if (!cur[(size_t)r * n + c]) continue;
+                const int d = abs(c - j);
+                if (c == j) T[nt++] = (btok_t){r, r, c};
+                else if (r < r0) T[nt++] = (btok_t){r - d, r, c};
+                else if (r >= r1) T[nt++] = (btok_t){r + d, r, c};
+            }
+        if (nt < h) { st = E_BUG; goto done; }
+        g_r0 = r0; g_r1 = r1; g_rcv = j; g_tie_bug = 0;
+        qsort(T, (size_t)nt, sizeof(btok_t), cmp_btok);
+        if (g_tie_bug) { st = E_BUG; goto done; }
+        for (int k = 0; k < nt; ++k) pos[k] = T[k].pos;
+        /* Generalised exact 1D: the optimal window gives how many tokens each
+         * vertex gives; a vertex holding several gives its nearest ones. */
+        const int w = rro_window(pos, nt, r0, h);
+        if (w < 0) { st = E_BUG; goto done; }
+        memset(take, 0, (size_t)nt);
+        int ntop = 0, nbot = 0;
+        for (int k = w; k < w + h;) {
+            int e = k;
+            while (e < w + h && pos[e] == pos[k]) ++e;     /* window part on this vertex */
+            int g0 = k, g1 = e;                            /* all tokens on this vertex */
+            while (g0 > 0 && pos[g0 - 1] == pos[k]) --g0;
+            while (g1 < nt && pos[g1] == pos[k]) ++g1;
+            const int want = e - k;
+            if (pos[k] < r0) for (int q = g1 - want; q < g1; ++q) take[q] = 1;
+            else for (int q = g0; q < g0 + want; ++q) take[q] = 1;
+            if (pos[k] < r0) ntop += want;
+            else if (pos[k] >= r1) nbot += want;
+            k = e;
+        }
+        int cnt = 0;
+        for (int k = 0; k < nt; ++k)
+            if (take[k]) { unit[cnt] = (mv_t){T[k].row, T[k].col, r0 + cnt, j}; ++cnt; }
+        if (cnt != h) { st = E_BUG; goto done; }
+        apply_unit(cur, n, unit, cnt);
+        if ((st = emit_unit(&out, unit, cnt)) != OK) goto done;
+        if (units && nu < cap_units) {
+            units[3 * nu] = j; units[3 * nu + 1] = ntop; units[3 * nu + 2] = nbot;
+        }
+        ++nu;
+    }
+
+done:
+    if (st == OK || st == INFEASIBLE) {
+        if (out.err) st = E_NOMEM;
+    }
+    if (st == OK || st == INFEASIBLE) {
+        *n_moves = out.n;
+        if (out.n > cap) st = E_CAP;
+        else if (out.n) memcpy(moves, out.v, sizeof(mv_t) * (size_t)out.n);
+    }
+    if (n_units) *n_units = nu;
+    free(cur); free(recv); free(rows); free(unit); free(T); free(pos); free(take); free(out.v);
     return st;
 }
 

@@ -1,7 +1,7 @@
 /*
  * rr_oracle.h -- sequential CPU oracle for the improved red-rec planner and
  * the batching routine of Afiouni et al., "Efficient algorithms to solve atom
- * reconfiguration problems III" (arXiv 2504.06182), Alg. 1 and Alg. 2.
+ * reconfiguration problems III" (arXiv 2504.06182), Alg. 1, 2 and 4.
  *
  * TEST INFRASTRUCTURE ONLY. The oracle is the slow, plain statement of what
  * the planner computes; the tests, the smoke check and the benchmark's CPU
@@ -30,7 +30,8 @@ extern "C" {
 #endif
 
 /* Optimal contiguous window (Sec. III.A, exact 1D with contiguous targets):
- * sources s[0..K) strictly increasing rows, targets r0 .. r0+h-1, K >= h.
+ * sources s[0..K) sorted ascending (repeats allowed: several tokens on one
+ * vertex, Sec. III.A "Generalized assignment"), targets r0 .. r0+h-1, K >= h.
  * Returns the window start w minimising sum_k |s[w+k] - (r0+k)|, smallest w on
  * ties; -1 on bad arguments. */
 int rro_window(const int32_t *s, int K, int r0, int h);
@@ -55,7 +56,16 @@ int rro_plan(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
              int32_t *sigma_out, int32_t *events, int64_t cap_ev,
              int64_t *n_events);
 
-/* The batching routine (Alg. 2 with the local constraint set of Sec. IV).
+/* The bird planner (Alg. 2, Sec. III.E): red-rec's column phase, then the
+ * unsolved columns left to right, each filled through its generalised 1D
+ * instance over every token of the grid. moves: cap*4 int32. units:
+ * cap_units*3 int32 (receiver column, tokens taken from above the band,
+ * tokens taken from below it) per receiver (may be NULL). */
+int rro_bird(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
+             int32_t *moves, int64_t cap, int64_t *n_moves,
+             int32_t *units, int64_t cap_units, int64_t *n_units);
+
+/* The batching routine (Alg. 4 with the local constraint set of Sec. IV).
  * ops: cap_ops*3 int32; members: cap_members int32. */
 int rro_batch(const int32_t *moves, int64_t n_moves, int m, int n,
               int32_t *ops, int64_t cap_ops, int32_t *members,

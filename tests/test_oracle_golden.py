@@ -1,7 +1,8 @@
 """The oracle against hand-worked instances (tests/golden/*.json).
 
-Each fixture was solved by hand from the rules of Alg. 1 / Sec. III.A-C and
-Alg. 2 / Sec. IV, with the derivation written in the file."""
+Each fixture was solved by hand from the rules of Alg. 1 / Sec. III.A-C,
+Alg. 2 / Sec. III.E (fixtures with "planner": "bird") and Alg. 4 / Sec. IV,
+with the derivation written in the file."""
 import glob
 import json
 import os
@@ -20,10 +21,14 @@ def test_golden(path):
     fx = json.load(open(path))
     grid = grid_from_rows(fx["grid"])
     rect = tuple(fx["rect"])
-    p = oracle.plan(grid, rect, with_trace=True)
+    if fx.get("planner") == "bird":
+        p = oracle.bird(grid, rect, with_trace=True)
+        assert p.events.tolist() == fx["units"]
+    else:
+        p = oracle.plan(grid, rect, with_trace=True)
+        assert p.events.tolist() == fx["events"]
     assert p.status == fx["status"]
     assert p.moves.tolist() == fx["moves"]
-    assert p.events.tolist() == fx["events"]
     ops, mem = oracle.batch(p.moves, *grid.shape)
     assert ops.tolist() == fx["ops"]
     assert mem.tolist() == fx["members"]
@@ -34,4 +39,4 @@ def test_golden(path):
 
 
 def test_golden_fixture_count():
-    assert len(GOLDEN) >= 5
+    assert len(GOLDEN) >= 8
