@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=1000,
                     help="requests of the served high-load run (0: skip the served runs)")
     ap.add_argument("--served-load", type=float, default=0.8, help="arrival rate as a fraction of saturation")
+    ap.add_argument("--no-bird", action="store_true", help="skip the bird planner's line")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch configuration (for profiling fixed launches)")
     ap.add_argument("--configs", action="store_true",
@@ -84,14 +85,15 @@ def dist_env():
 
 # ------------------------------------------------------------------ oracle
 
-def oracle_sample(insts, budget_s, threads):
-    """Plan + batch grids in order with the CPU oracle on `threads` host
-    threads until the time budget is spent. Returns (grids done, seconds)."""
+def oracle_sample(insts, budget_s, threads, bird=False):
+    """Plan (red-rec, or bird) + batch grids in order with the CPU oracle on
+    `threads` host threads until the time budget is spent. Returns (grids
+    done, seconds)."""
     import oracle
     oracle.build()
 
     def one(inst):
-        p = oracle.plan(inst.grid, inst.rect)
+        p = (oracle.bird if bird else oracle.plan)(inst.grid, inst.rect)
         if p.status == 0:
             oracle.batch(p.moves, *inst.grid.shape)
         return 1
@@ -219,7 +221,8 @@ def median_us(fn, reps):
 
 
 def oracle_paper_geometry():
-    """Single-thread oracle latency per grid at the paper's geometry."""
+    """Single-thread oracle latency per grid at the paper's geometry (red-rec
+    plan, plan + batching, and the bird plan)."""
     import oracle
     oracle.build()
     res = {}
@@ -228,7 +231,8 @@ def oracle_paper_geometry():
         plan_us = median_us(lambda: oracle.plan(inst.grid, inst.rect), reps)
         p = oracle.plan(inst.grid, inst.rect)
         both_us = median_us(lambda: oracle.batch(p.moves, *inst.grid.shape), reps) + plan_us
-        res[str(inst.grid.shape[1])] = {"plan_us": plan_us, "plan_batch_us": both_us}
+        bird_us = median_us(lambda: oracle.bird(inst.grid, inst.rect), reps)
+        res[str(inst.grid.shape[1])] = {"plan_us": plan_us, "plan_batch_us": both_us, "bird_plan_us": bird_us}
     return res
 
 
@@ -243,8 +247,8 @@ def gpu_paper_geometry(rr, P):
         g = torch.from_numpy(np.ascontiguousarray(gridgen.pack_bits32(inst.grid).view(np.int32))).cuda()
         cap = 2 * m * n
 
-        def plan():
-            return P.plan(g, inst.rect, layout=rr.RR_BITS32, n=n, cap=cap)
+        def plan(bird=False):
+            return P.plan(g, inst.rect, layout=rr.RR_BITS32, n=n, cap=cap, bird=bird)
 
         def both():
             st, mv = plan()
@@ -253,9 +257,113 @@ def gpu_paper_geometry(rr, P):
             torch.cuda.synchronize()
         for _ in range(3):
             both()
+            plan(True)
         reps = 50 if n <= 64 else 10
-        res[str(n)] = {"plan_us": median_us(plan, reps), "plan_batch_us": median_us(both, reps)}
+        res[str(n)] = {"plan_us": median_us(plan, reps), "plan_batch_us": median_us(both, reps),
+                       "bird_plan_us": median_us(lambda: plan(True), reps)}
     return res
+
+
+# ------------------------------------------------------------------ batched
+
+def make_entries(rr, insts, grids, offs, sides, moves=None, ops=None, mem=None, caps=None):
+    """Descriptors of the workload's grids (slices of one packed device
+    buffer), with output slices of shared buffers when `caps` is given:
+    per grid (cap moves, cap ops, cap members, move, op, member offsets)."""
+    out = []
+    for g, inst in enumerate(insts):
+        s = sides[g]
+        e = dict(grid=grids[offs[g]:offs[g + 1]], layout=rr.RR_BITS32, m=s, n=s, rect=inst.rect)
+        if caps is not None:
+            cm, co, cs, om, oo, os_ = caps[g]
+            e.update(moves=moves[om:om + 1] if cm else None, cap_moves=cm,
+                     ops=ops[oo:oo + 1] if co else None, cap_ops=co,
+                     members=mem[os_:os_ + 1] if cs else None, cap_members=cs)
+        out.append(e)
+    return out
+
+
+def sized_descriptors(rr, P, insts, grids, offs, sides, extra_flags=0):
+    """Sizes every grid's outputs on the device (a planning pass without
+    output room gives the move counts, a planning + batching pass the step
+    counts), allocates them and returns (descriptors, moves, ops, members)."""
+    import torch
+    from paper_2504_06182_gb300.planner import pack_instances, unpack_instances
+    count, max_side, dev = len(insts), max(sides), grids.device
+    d_inst = pack_instances(make_entries(rr, insts, grids, offs, sides))
+    rr.rr_plan_batched(P.ctx, d_inst, count, max_side, extra_flags)
+    torch.cuda.synchronize()
+    n_moves = np.array([x.n_moves for x in unpack_instances(d_inst, count)], dtype=np.int64)
+    moves = torch.empty((int(n_moves.sum()) + 1, 4), dtype=torch.int32, device=dev)
+    mo = np.concatenate([[0], np.cumsum(n_moves)])
+    caps = [(int(n_moves[g]), 0, 0, int(mo[g]), 0, 0) for g in range(count)]
+    d_inst = pack_instances(make_entries(rr, insts, grids, offs, sides, moves, None, None, caps))
+    rr.rr_plan_batched(P.ctx, d_inst, count, max_side, rr.RR_WITH_BATCH | extra_flags)
+    torch.cuda.synchronize()
+    n_steps = np.array([x.n_steps for x in unpack_instances(d_inst, count)], dtype=np.int64)
+    so = np.concatenate([[0], np.cumsum(n_steps)])
+    ops = torch.empty((int(n_steps.sum()) + 1, 3), dtype=torch.int32, device=dev)
+    mem = torch.empty((int(n_steps.sum()) + 1,), dtype=torch.int32, device=dev)
+    caps = [(int(n_moves[g]), int(n_steps[g]), int(n_steps[g]), int(mo[g]), int(so[g]), int(so[g]))
+            for g in range(count)]
+    d_inst = pack_instances(make_entries(rr, insts, grids, offs, sides, moves, ops, mem, caps))
+    return d_inst, moves, ops, mem
+
+
+def run_bird(args, rr, P, insts, grids, offs, sides, flush, cpu_threads):
+    """The bird planner (Alg. 2) with batching on the same resident grids:
+    one rr_plan_batched(RR_WITH_BATCH | RR_BIRD) call per step, L2 flushed
+    between steps, CUDA events on the launching stream; its per-stage times;
+    its control-operation counts next to red-rec's; the CPU oracle (bird +
+    batching) on a bounded sample of the same grids."""
+    import torch
+    from paper_2504_06182_gb300.planner import unpack_instances
+    count, max_side = len(insts), max(sides)
+    flags = rr.RR_WITH_BATCH | rr.RR_BIRD
+    d_inst, moves, ops, mem = sized_descriptors(rr, P, insts, grids, offs, sides, rr.RR_BIRD)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        rr.rr_plan_batched(P.ctx, d_inst, count, max_side, flags, stream)
+    torch.cuda.synchronize()
+    rr.rr_set_tracing(P.ctx, True)
+    times, stage_tot = [], {}
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = rr.rr_plan_batched(P.ctx, d_inst, count, max_side, flags, stream)
+        b.record(stream)
+        b.synchronize()
+        if st != rr.RR_OK:
+            raise rr.RRError(st, rr.rr_last_error(P.ctx))
+        times.append(a.elapsed_time(b))
+        for nm, ms in rr.rr_stage_times(P.ctx):
+            stage_tot[nm] = stage_tot.get(nm, 0.0) + ms
+    rr.rr_set_tracing(P.ctx, False)
+    res = unpack_instances(d_inst, count)
+    bad = [(g, x.status) for g, x in enumerate(res) if x.status not in (rr.RR_OK, rr.RR_INFEASIBLE)]
+    if bad:
+        raise RuntimeError(f"bird instances failed: {bad[:5]}")
+    feasible = sum(x.status == rr.RR_OK for x in res)
+    tot_moves = sum(x.n_moves for x in res)
+    tot_ops = sum(x.n_ops for x in res)
+    tot_mem = sum(x.n_members for x in res)
+    del moves, ops, mem
+    cpu = None
+    if not args.no_cpu_baseline:
+        done, secs = oracle_sample(insts, min(args.cpu_budget, 10.0), cpu_threads, bird=True)
+        cpu = {"value": done / secs, "unit": "grids/s", "cores": cpu_threads, "kind": "oracle",
+               "sample": f"first {done} grids of the workload (bird + batching), {cpu_threads} host threads, "
+                         f"{secs:.1f} s"}
+    total_ms = float(sum(times))
+    return {"value": count * args.steps / (total_ms * 1e-3), "unit": "grids/s",
+            "ms_per_step": total_ms / args.steps,
+            "note": "the same grids planned with bird (Alg. 2) and batched, one rr_plan_batched call per step",
+            "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_tot.items(), key=lambda kv: -kv[1])},
+            "control_ops_per_feasible_grid": {
+                "N_nu": tot_mem / max(1, feasible), "N_alpha": 2 * tot_moves / max(1, feasible),
+                "NB_nu": tot_ops / max(1, feasible), "N_nu_per_NB_nu": tot_mem / max(1, tot_ops)},
+            "feasible": int(feasible), "cpu_baseline": cpu}
 
 
 # ------------------------------------------------------------------ plain
@@ -418,7 +526,7 @@ def run_served(rr, requests, load, seed=5, slots=256, streams=32, max_wave=8, pl
 def run_ours(args, rank, world, local):
     import torch
     import paper_2504_06182_gb300 as rr
-    from paper_2504_06182_gb300.planner import Planner, pack_instances, unpack_instances
+    from paper_2504_06182_gb300.planner import Planner, unpack_instances
 
     insts = gridgen.mixed_instances(rank_seed(args.seed, rank), args.count)
     # CPU oracle baseline on host cores before any GPU work (rank 0, N = 1)
@@ -448,40 +556,7 @@ def run_ours(args, rank, world, local):
     max_side = max(sides)
 
     P = Planner(arena_bytes=int(os.environ.get("RR_ARENA_GB", "24")) << 30)
-
-    def entries(moves=None, ops=None, mem=None, caps=None):
-        out = []
-        for g, inst in enumerate(insts):
-            s = sides[g]
-            e = dict(grid=grids[offs[g]:offs[g + 1]], layout=rr.RR_BITS32, m=s, n=s, rect=inst.rect)
-            if caps is not None:
-                cm, co, cs, om, oo, os_ = caps[g]
-                e.update(moves=moves[om:om + 1] if cm else None, cap_moves=cm,
-                         ops=ops[oo:oo + 1] if co else None, cap_ops=co,
-                         members=mem[os_:os_ + 1] if cs else None, cap_members=cs)
-            out.append(e)
-        return out
-
-    # sizing: plan with no output room gives the move counts
-    d_inst = pack_instances(entries())
-    rr.rr_plan_batched(P.ctx, d_inst, count, max_side, 0)
-    torch.cuda.synchronize()
-    r = unpack_instances(d_inst, count)
-    n_moves = np.array([x.n_moves for x in r], dtype=np.int64)
-    moves = torch.empty((int(n_moves.sum()) + 1, 4), dtype=torch.int32, device=dev)
-    mo = np.concatenate([[0], np.cumsum(n_moves)])
-    caps = [(int(n_moves[g]), 0, 0, int(mo[g]), 0, 0) for g in range(count)]
-    d_inst = pack_instances(entries(moves, None, None, caps))
-    rr.rr_plan_batched(P.ctx, d_inst, count, max_side, rr.RR_WITH_BATCH)
-    torch.cuda.synchronize()
-    r = unpack_instances(d_inst, count)
-    n_steps = np.array([x.n_steps for x in r], dtype=np.int64)
-    so = np.concatenate([[0], np.cumsum(n_steps)])
-    ops = torch.empty((int(n_steps.sum()) + 1, 3), dtype=torch.int32, device=dev)
-    mem = torch.empty((int(n_steps.sum()) + 1,), dtype=torch.int32, device=dev)
-    caps = [(int(n_moves[g]), int(n_steps[g]), int(n_steps[g]), int(mo[g]), int(so[g]), int(so[g]))
-            for g in range(count)]
-    d_inst = pack_instances(entries(moves, ops, mem, caps))
+    d_inst, moves, ops, mem = sized_descriptors(rr, P, insts, grids, offs, sides)
     inst_host = d_inst.cpu().pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
@@ -583,6 +658,8 @@ def run_ours(args, rank, world, local):
              "geometry": "n_tx columns, ceil(n_tx/0.6) rows, full-width target of n_tx rows, p = 0.6"} \
         if args.plain_sample > 0 else None
     del ops, mem, moves
+    bird = run_bird(args, rr, P, insts, grids, offs, sides, flush, os.cpu_count() or 1) \
+        if not args.no_bird else None
     P.close()
     torch.cuda.empty_cache()
     served = run_served(rr, args.served_requests, args.served_load) if args.served_requests > 0 else None
@@ -636,6 +713,7 @@ def run_ours(args, rank, world, local):
         "plain": plain,
         "paper_geometry": paper,
         "served": served,
+        "bird": bird,
         "clocks": clk,
         "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_tot.items(), key=lambda kv: -kv[1])},
         "totals_per_step": {"moves": int(tot_moves), "ops": int(tot_ops), "steps": int(tot_mem),

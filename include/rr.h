@@ -74,6 +74,21 @@ int rr_ctx_destroy(rr_ctx *ctx);
 int rr_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect,
             rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream);
 
+/* Plan one grid with the bird algorithm (Alg. 2, Sec. III.E). Arguments,
+ * layouts, output and synchronisation as rr_plan. The column phase is
+ * rr_plan's (the same moves, first); then the columns of negative surplus are
+ * filled one by one, left to right, each through its generalised 1D instance:
+ * the column's own atoms plus every atom in a reservoir row (a row outside
+ * [r0, r1)) of every other column, an atom at column distance d standing on
+ * vertex row - d (above the band) or row + d (below it) of the column. The
+ * tokens of least total distance are taken (a vertex holding several gives
+ * its nearest columns' tokens, left before right), matched in order and
+ * emitted as one unit with rr_plan's order inside a unit. The paper states
+ * bird for centred targets; nothing here needs the centring. Feasibility is
+ * rr_plan's (RR_INFEASIBLE iff the total surplus is negative). */
+int rr_bird_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect,
+                 rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream);
+
 /* Batch a move list (Alg. 4 + Sec. IV): dependencies = every earlier move
  * whose path shares a vertex; ready moves are visited in ascending id and a
  * move's next step joins the batch iff it has the first member's direction and
@@ -96,6 +111,7 @@ int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, int m, int n,
 #define RR_WITH_BATCH 1
 #define RR_BATCH_ONLY 2   /* skip planning: instances carry moves and n_moves (status RR_OK) */
 #define RR_GRAPH 4        /* replay a captured CUDA graph of the launch sequence (below) */
+#define RR_BIRD 8         /* plan with the bird algorithm (as rr_bird_plan) instead of red-rec */
 typedef struct {
     const void *grid;
     int32_t layout, m, n, pad0;
@@ -179,7 +195,7 @@ typedef struct {
     int32_t slots;           /* requests admitted and not yet released, at most */
     int32_t streams;         /* waves in flight at once */
     int32_t max_wave;        /* requests per wave, <= slots */
-    int32_t flags;           /* RR_WITH_BATCH to also batch every plan */
+    int32_t flags;           /* RR_WITH_BATCH to also batch every plan; RR_BIRD to plan with bird */
     int32_t pad;
     int64_t arena_bytes;     /* workspace arena per stream */
     int64_t heap_bytes;      /* device heap for batch results (16 B per elementary step) */

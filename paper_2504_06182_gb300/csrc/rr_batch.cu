@@ -25,8 +25,6 @@
 
 namespace rrk {
 
-__device__ __forceinline__ bool live(const rr_instance *I) { return I->status == RR_OK; }
-
 // Chunked block-wide exclusive scan of v[0..len) in place; returns the total.
 // Every thread of the block must call it.
 __device__ long long block_exclusive_scan(int32_t *v, int len, long long *s_tmp /* >= 33 */)

@@ -14,6 +14,7 @@ __global__ void k_colstats(rr_instance *, JobWS *, int);
 __global__ void k_pair(rr_instance *, JobWS *, int);
 __global__ void k_emit_cols(rr_instance *, JobWS *, int);
 __global__ void k_emit_recv(rr_instance *, JobWS *, int);
+__global__ void k_bird(rr_instance *, JobWS *, int, int);
 __global__ void k_bsetup(rr_instance *, JobWS *, int, Arena);
 __global__ void k_gcount(rr_instance *, JobWS *, int);
 __global__ void k_gscan(rr_instance *, JobWS *, int);
@@ -46,7 +47,7 @@ static_assert(sizeof(rr_instance) == 128, "rr_instance layout is part of the ABI
 static constexpr int SMALL_CALL = 8;
 
 // Kernels launched with more than the default 48 KB of dynamic shared memory.
-enum { SM_GSORT, SM_GSWEEP_H, SM_GSWEEP_V, SM_SIM16, SM_SIM32, SM_SIM16W, SM_SIM32W, SM_NKERNEL };
+enum { SM_GSORT, SM_GSWEEP_H, SM_GSWEEP_V, SM_SIM16, SM_SIM32, SM_SIM16W, SM_SIM32W, SM_BIRD, SM_NKERNEL };
 
 struct rr_ctx {
     int device;
@@ -140,7 +141,7 @@ static int smem_limits(int dev, int *out)
         cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         const void *fn[SM_NKERNEL] = {(const void *)k_gsort, (const void *)k_gsweep_h, (const void *)k_gsweep_v,
                                       (const void *)k_sim16, (const void *)k_sim32, (const void *)k_sim16w,
-                                      (const void *)k_sim32w};
+                                      (const void *)k_sim32w, (const void *)k_bird};
         for (int i = 0; e == cudaSuccess && i < SM_NKERNEL; ++i) {
             cudaFuncAttributes fa;
             e = cudaFuncGetAttributes(&fa, fn[i]);
@@ -294,8 +295,18 @@ static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v
 // Blocks a launch may spread over all grids of a call (divided by the count).
 static int budget(const rr_ctx *ctx, int base) { return ctx->shift >= 0 ? base << ctx->shift : base >> -ctx->shift; }
 
-// Planning kernels over `count` device descriptors whose sides are <= max_side.
-static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, int max_side, cudaStream_t s)
+// Shared memory of a k_bird block: reservoir-row bits of the largest grid
+// (column-major, one word per 32 rows) and the two walk lists.
+static size_t bird_smem_bytes(int max_side)
+{
+    return 4 * ((size_t)max_side * ((max_side + 31) / 32) + 2 * (size_t)max_side);
+}
+
+// Planning kernels over `count` device descriptors whose sides are <= max_side:
+// red-rec (Alg. 1), or with `bird` the bird algorithm (Alg. 2), which shares
+// red-rec's column phase.
+static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, int max_side, cudaStream_t s,
+                       bool bird)
 {
     const Arena A = arena_of(ctx);
     const int colBlocks = clampi(std::max(1, budget(ctx, 4096) / count), 1, (max_side + 7) / 8);
@@ -308,6 +319,19 @@ static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, i
     k_transpose<<<dim3(trBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_colstats");
     k_colstats<<<dim3(colBlocks, count), 256, 0, s>>>(d_inst, ws, count);
+    if (bird) {
+        const size_t birdSmem = bird_smem_bytes(max_side);
+        if (birdSmem > (size_t)ctx->smemLimit[SM_BIRD])
+            return fail(ctx, RR_ERR_ARG, "bird: shared memory %zu for side %d too large", birdSmem, max_side);
+        mark(ctx, s, "k_bird");
+        k_bird<<<count, 64, birdSmem, s>>>(d_inst, ws, count, max_side);
+        mark(ctx, s, "k_emit_cols");
+        k_emit_cols<<<dim3(colBlocks, count), 256, 0, s>>>(d_inst, ws, count);
+        mark(ctx, s, nullptr);
+        CUDA_TRY(cudaGetLastError());
+        ctx->nlaunch += 5;
+        return RR_OK;
+    }
     const size_t pairSmem = (size_t)max_side * 30 + 64;
     mark(ctx, s, "k_pair");
     k_pair<<<count, 32, pairSmem, s>>>(d_inst, ws, count);
@@ -432,13 +456,14 @@ static bool rect_ok(int m, int n, rr_rect R)
            R.r1 <= m && R.c0 >= 0 && R.c0 < R.c1 && R.c1 <= n;
 }
 
-extern "C" int rr_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect,
-                       rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream)
+static int plan_one(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect, rr_move *d_moves,
+                    int64_t cap, int64_t *n_moves, cudaStream_t stream, bool bird)
 {
+    const char *name = bird ? "rr_bird_plan" : "rr_plan";
     if (!ctx || !d_grid || !n_moves || (layout != RR_U8 && layout != RR_BITS32) || !rect_ok(m, n, rect) ||
         cap < 0 || (cap > 0 && !d_moves))
-        return fail(ctx, RR_ERR_ARG, "rr_plan: bad argument (m=%d n=%d rect=[%d,%d,%d,%d] layout=%d cap=%lld)", m, n,
-                    rect.r0, rect.c0, rect.r1, rect.c1, layout, (long long)cap);
+        return fail(ctx, RR_ERR_ARG, "%s: bad argument (m=%d n=%d rect=[%d,%d,%d,%d] layout=%d cap=%lld)", name, m,
+                    n, rect.r0, rect.c0, rect.r1, rect.c1, layout, (long long)cap);
     rr_instance h;
     std::memset(&h, 0, sizeof(h));
     h.grid = d_grid; h.layout = layout; h.m = m; h.n = n; h.rect = rect;
@@ -446,13 +471,26 @@ extern "C" int rr_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n
     ctx->nmarks = 0;
     CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->d_one, &h, sizeof(h), cudaMemcpyHostToDevice, stream));
-    int st = launch_plan(ctx, ctx->d_one, ctx->d_ws, 1, std::max(m, n), stream);
+    int st = launch_plan(ctx, ctx->d_one, ctx->d_ws, 1, std::max(m, n), stream, bird);
     if (st != RR_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(&h, ctx->d_one, sizeof(h), cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaStreamSynchronize(stream));
     *n_moves = h.n_moves;
-    if (h.status < 0) return fail(ctx, h.status, "rr_plan: device status %d (n_moves=%lld)", h.status, (long long)h.n_moves);
+    if (h.status < 0)
+        return fail(ctx, h.status, "%s: device status %d (n_moves=%lld)", name, h.status, (long long)h.n_moves);
     return h.status;
+}
+
+extern "C" int rr_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect,
+                       rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream)
+{
+    return plan_one(ctx, d_grid, layout, m, n, rect, d_moves, cap, n_moves, stream, false);
+}
+
+extern "C" int rr_bird_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect,
+                            rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream)
+{
+    return plan_one(ctx, d_grid, layout, m, n, rect, d_moves, cap, n_moves, stream, true);
 }
 
 extern "C" int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, int m, int n, rr_op *d_ops,
@@ -511,9 +549,10 @@ static int launch_sequence(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
 {
     CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
     const bool plan = !(flags & RR_BATCH_ONLY), batch = (flags & (RR_WITH_BATCH | RR_BATCH_ONLY)) != 0;
+    const bool bird = (flags & RR_BIRD) != 0;
     const int *frac = PIPE_FRAC64[ctx->pipe > 0 && ctx->pipe < PIPE_SPLITS ? ctx->pipe : 0];
     if (!batch || frac[0] == 0 || count < PIPE_MIN) {
-        int st = plan ? launch_plan(ctx, d_inst, ctx->d_ws, count, max_side, stream) : RR_OK;
+        int st = plan ? launch_plan(ctx, d_inst, ctx->d_ws, count, max_side, stream, bird) : RR_OK;
         if (st == RR_OK && batch)
             st = launch_batch(ctx, d_inst, ctx->d_ws, count, max_side, stream, SIM_CLASSES, nullptr, nullptr);
         return st;
@@ -531,7 +570,7 @@ static int launch_sequence(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
         cudaStream_t gs = ctx->leadStream[g];
         CUDA_TRY(cudaStreamWaitEvent(gs, ctx->evStart, 0));
         ctx->quiet = g > 0;                  // stage marks follow the first group
-        if (plan) st = launch_plan(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, hi - lo, max_side, gs);
+        if (plan) st = launch_plan(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, hi - lo, max_side, gs, bird);
         if (st == RR_OK)
             st = launch_batch(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, hi - lo, max_side, gs, SIM_ONE, prevSim,
                               ctx->evSim[g]);
@@ -547,7 +586,7 @@ static int launch_sequence(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
     if (st == RR_OK) {
         cudaStream_t rs = ctx->restStream;
         CUDA_TRY(cudaStreamWaitEvent(rs, ctx->evStart, 0));
-        if (plan) st = launch_plan(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, count - lo, max_side, rs);
+        if (plan) st = launch_plan(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, count - lo, max_side, rs, bird);
         if (st == RR_OK)
             st = launch_batch(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, count - lo, max_side, rs, SIM_CLASSES, prevSim,
                               nullptr);
@@ -569,7 +608,7 @@ extern "C" int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int 
                                cudaStream_t stream)
 {
     if (!ctx || !d_inst || count < 1 || count > 65535 || max_side < 1 || max_side > RR_MAX_SIDE ||
-        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY | RR_GRAPH)))
+        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY | RR_GRAPH | RR_BIRD)))
         return fail(ctx, RR_ERR_ARG, "rr_plan_batched: bad argument (count=%d max_side=%d flags=%d)", count,
                     max_side, flags);
     int st = ensure_ws(ctx, count);
@@ -616,7 +655,7 @@ extern "C" int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
                            cudaStream_t stream, int32_t *nclass, int32_t *shift, int32_t *pipe)
 {
     if (!ctx || !d_inst || count < 1 || count > 65535 || max_side < 1 || max_side > RR_MAX_SIDE ||
-        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY)))
+        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY | RR_BIRD)))
         return fail(ctx, RR_ERR_ARG, "rr_autotune: bad argument (count=%d max_side=%d flags=%d)", count, max_side,
                     flags);
     int st = ensure_ws(ctx, count);

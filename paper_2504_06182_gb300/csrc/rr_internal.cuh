@@ -192,6 +192,51 @@ __device__ __forceinline__ void set_status(rr_instance *I, int st)
 {
     atomicCAS(&I->status, 0, st);
 }
+__device__ __forceinline__ bool live(const rr_instance *I) { return I->status == RR_OK; }
+
+// Adds a warp's elementary-step count to the instance total (every lane of
+// the warp calls it).
+__device__ __forceinline__ void add_steps(rr_instance *I, long long v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long *)&I->n_steps, (unsigned long long)v);
+}
+
+// Largest a in [lo, hi] with a == lo or delta(a) <= 0, for a non-decreasing
+// delta (the discrete derivative of a convex cost). Warp-cooperative: every
+// round probes 32 evenly spaced candidates.
+template <class F>
+__device__ int split_search(int lo, int hi, F delta)
+{
+    const int lane = threadIdx.x & 31;
+    for (int guard = 0; hi > lo && guard < 8; ++guard) {
+        const int span = hi - lo;
+        const int al = lo + (int)(((long long)(lane + 1) * span + 31) / 32);
+        const bool ok = delta(al) <= 0;
+        const unsigned bal = __ballot_sync(FULL, ok);
+        if (bal == 0u) {
+            hi = __shfl_sync(FULL, al, 0) - 1;
+        } else {
+            const int L = 31 - __clz(bal);
+            const int aL = __shfl_sync(FULL, al, L);
+            const int aN = __shfl_sync(FULL, al, L < 31 ? L + 1 : 31);
+            lo = aL;
+            if (L < 31) hi = aN - 1;
+        }
+    }
+    return lo;
+}
+
+// Number of band atoms i of a target column with (b_i - i) <= T, i.e. with at
+// most T - r0 empty band traps above them. hr: the column's band holes.
+__device__ __forceinline__ int band_P(const int16_t *hr, int nh, int nband, int r0, int T)
+{
+    const int u = T - r0;
+    if (u < 0) return 0;
+    if (u >= nh) return nband;
+    return (int)hr[u] - r0 - u;
+}
 
 } // namespace rrk
 

@@ -1,0 +1,183 @@
+"""The bird planner (Alg. 2, Sec. III.E) on the GPU against the oracle,
+element by element (bit-exact), through the C ABI: single grids in both
+layouts from tiny random rectangles to 256 x 256, the paper's runtime
+geometry, mixed 32..256 grids through the batched entry point (planning and
+batching, pipelined), and a 1024 x 1024 grid checked by replay."""
+import numpy as np
+import pytest
+
+import gridgen
+import oracle
+from tests.checks import replay_moves, assert_target_full
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def planner():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_06182_gb300.planner import Planner
+    p = Planner(arena_bytes=4 << 30)
+    yield p
+    p.close()
+
+
+def to_device(grid, layout):
+    from paper_2504_06182_gb300 import RR_U8
+    if layout == RR_U8:
+        return torch.from_numpy(np.ascontiguousarray(grid)).cuda()
+    words = gridgen.pack_bits32(grid).view(np.int32)
+    return torch.from_numpy(np.ascontiguousarray(words)).cuda()
+
+
+def check_bird(planner, grid, rect, layout, with_batch=True):
+    ref = oracle.bird(grid, rect)
+    m, n = grid.shape
+    st, mv = planner.plan(to_device(grid, layout), rect, layout=layout, n=n, bird=True)
+    mv = mv.cpu().numpy()
+    assert st == ref.status, (st, ref.status, grid.shape, rect)
+    assert mv.shape == ref.moves.shape, (mv.shape, ref.moves.shape)
+    if len(mv):
+        bad = np.nonzero((mv != ref.moves).any(axis=1))[0]
+        assert len(bad) == 0, f"first mismatch at move {bad[0]}: gpu {mv[bad[0]]} oracle {ref.moves[bad[0]]}"
+    if with_batch and ref.status == 0:
+        rops, rmem = oracle.batch(ref.moves, m, n)
+        ops, mem = planner.batch(torch.from_numpy(ref.moves).cuda(), m, n)
+        assert (ops.cpu().numpy() == rops).all() and ops.shape[0] == len(rops)
+        assert (mem.cpu().numpy() == rmem).all() and mem.shape[0] == len(rmem)
+    return ref
+
+
+def random_case(rng):
+    m = int(rng.integers(1, 70))
+    n = int(rng.integers(1, 70))
+    grid = (rng.random((m, n)) < rng.uniform(0.2, 0.95)).astype(np.uint8)
+    h = int(rng.integers(1, m + 1))
+    r0 = int(rng.integers(0, m - h + 1))
+    w = int(rng.integers(1, n + 1))
+    c0 = int(rng.integers(0, n - w + 1))
+    return grid, (r0, c0, r0 + h, c0 + w)
+
+
+def test_bird_random_small_grids(planner):
+    from paper_2504_06182_gb300 import RR_BITS32, RR_U8
+    rng = np.random.default_rng(4321)
+    feasible = with_recv = 0
+    for trial in range(400):
+        grid, rect = random_case(rng)
+        ref = check_bird(planner, grid, rect, RR_U8 if trial % 2 else RR_BITS32, with_batch=trial % 4 == 0)
+        feasible += ref.status == 0
+        r0, c0, r1, c1 = rect
+        with_recv += ref.status == 0 and any(grid[:, c].sum() < r1 - r0 for c in range(c0, c1))
+    assert feasible > 100 and with_recv > 50
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_bird_grid_32(planner, seed):
+    from paper_2504_06182_gb300 import RR_U8
+    inst = gridgen.square_instance(seed, 0, 32, 0.6, 20)
+    check_bird(planner, inst.grid, inst.rect, RR_U8)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bird_grid_256(planner, seed):
+    from paper_2504_06182_gb300 import RR_BITS32
+    inst = gridgen.square_instance(seed, 0, 256, 0.6, 180)
+    ref = check_bird(planner, inst.grid, inst.rect, RR_BITS32, with_batch=seed == 0)
+    assert ref.status == 0
+
+
+@pytest.mark.parametrize("n_tx", [32, 64, 128])
+def test_bird_paper_geometry(planner, n_tx):
+    """The paper's runtime geometry (full-width target of n_tx rows in
+    ceil(n_tx / 0.6) rows): a feasible and an infeasible instance."""
+    from paper_2504_06182_gb300 import RR_BITS32, RR_U8
+    seen = set()
+    for g in range(40):
+        inst = gridgen.paper_instance(41, g, n_tx)
+        ref = oracle.bird(inst.grid, inst.rect)
+        if ref.status in seen:
+            continue
+        seen.add(ref.status)
+        check_bird(planner, inst.grid, inst.rect, RR_U8)
+        check_bird(planner, inst.grid, inst.rect, RR_BITS32, with_batch=False)
+        if len(seen) == 2:
+            break
+    assert seen == {0, 1}
+
+
+@pytest.mark.parametrize("count", [48, 300])
+def test_bird_batched_mixed(planner, count):
+    """Mixed 32..256 grids through rr_plan_batched with RR_BIRD and batching
+    (300 grids run pipelined by size), each grid against the oracle."""
+    import paper_2504_06182_gb300 as rr
+    from paper_2504_06182_gb300.planner import pack_instances, plan_batched, unpack_instances
+    insts = gridgen.mixed_instances(17, count)
+    refs = [oracle.bird(i.grid, i.rect) for i in insts]
+    entries, outs = [], []
+    for inst, ref in zip(insts, refs):
+        s = inst.grid.shape[0]
+        k = max(len(ref.moves), 1)
+        mvs = ref.moves
+        steps = int((np.abs(mvs[:, 0] - mvs[:, 2]) + np.abs(mvs[:, 1] - mvs[:, 3])).sum()) if len(mvs) else 0
+        mv = torch.empty((k, 4), dtype=torch.int32, device="cuda")
+        ops = torch.empty((max(steps, 1), 3), dtype=torch.int32, device="cuda")
+        mem = torch.empty((max(steps, 1),), dtype=torch.int32, device="cuda")
+        entries.append(dict(grid=to_device(inst.grid, rr.RR_BITS32), layout=rr.RR_BITS32, m=s, n=s, rect=inst.rect,
+                            moves=mv, cap_moves=k, ops=ops, cap_ops=max(steps, 1), members=mem,
+                            cap_members=max(steps, 1)))
+        outs.append((mv, ops, mem))
+    dev = pack_instances(entries)
+    plan_batched(planner, dev, len(entries), 256, with_batch=True, bird=True)
+    torch.cuda.synchronize()
+    res = unpack_instances(dev, len(entries))
+    nbatched = 0
+    for inst, ref, r, (mv, ops, mem) in zip(insts, refs, res, outs):
+        assert r.status == (rr.RR_OK if ref.status == 0 else rr.RR_INFEASIBLE), r.status
+        assert r.n_moves == len(ref.moves)
+        if ref.status != 0:
+            continue
+        assert (mv[: r.n_moves].cpu().numpy() == ref.moves).all()
+        if nbatched < 60:
+            rops, rmem = oracle.batch(ref.moves, *inst.grid.shape)
+            assert r.n_ops == len(rops) and r.n_members == len(rmem)
+            assert (ops[: r.n_ops].cpu().numpy() == rops).all()
+            assert (mem[: r.n_members].cpu().numpy() == rmem).all()
+            nbatched += 1
+    assert nbatched > 10
+
+
+def test_bird_capacity_and_infeasible(planner):
+    import paper_2504_06182_gb300 as rr
+    inst = gridgen.square_instance(3, 0, 64, 0.6, 44)
+    ref = oracle.bird(inst.grid, inst.rect)
+    assert ref.status == 0 and len(ref.moves) > 10
+    g = to_device(inst.grid, rr.RR_U8)
+    small = torch.empty((5, 4), dtype=torch.int32, device="cuda")
+    st, k = rr.rr_bird_plan(planner.ctx, g, rr.RR_U8, 64, 64, inst.rect, small, 5)
+    assert st == rr.RR_ERR_CAPACITY and k == len(ref.moves)
+    empty = torch.zeros((16, 16), dtype=torch.uint8, device="cuda")
+    st, k = rr.rr_bird_plan(planner.ctx, empty, rr.RR_U8, 16, 16, (4, 4, 12, 12), small, 5)
+    assert st == rr.RR_INFEASIBLE and k == 0
+
+
+def test_bird_grid_1024_replay(planner):
+    """Full-size 1024 x 1024 grid with a centred 720 x 720 target (too large
+    for the oracle's literal window scan): the GPU's bird plan starts with
+    red-rec's column phase (itself equal to the oracle's), replays without
+    obstruction and fills the target."""
+    from paper_2504_06182_gb300 import RR_BITS32
+    inst = gridgen.square_instance(0, 0, 1024, 0.6, 720)
+    g = to_device(inst.grid, RR_BITS32)
+    st, mv = planner.plan(g, inst.rect, layout=RR_BITS32, n=1024, bird=True)
+    st2, rmv = planner.plan(g, inst.rect, layout=RR_BITS32, n=1024)
+    assert st == st2 == 0
+    mv, rmv = mv.cpu().numpy(), rmv.cpu().numpy()
+    ncol = int(np.argmax(rmv[:, 1] != rmv[:, 3])) if (rmv[:, 1] != rmv[:, 3]).any() else len(rmv)
+    ncol = min(ncol, int(np.argmax(mv[:, 1] != mv[:, 3])))
+    assert (mv[:ncol] == rmv[:ncol]).all()
+    final = replay_moves(inst.grid, inst.rect, mv)
+    assert_target_full(final, inst.rect, inst.grid)
