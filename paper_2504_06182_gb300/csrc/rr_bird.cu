@@ -36,40 +36,151 @@ __device__ __forceinline__ int isqrt_floor(int g)
     return k;
 }
 
-// Collects, nearest first, up to `need` tokens of receiver j on one side of
-// the band (one warp). Cell g of the walk is layer k = floor(sqrt(g)), index
-// i = g - k*k in it: i = 0 is column j itself, i = 2d-1 column j-d, i = 2d
-// column j+d, on row r0-1-k+d above the band or r1+k-d below it.
-__device__ int bird_walk(const uint32_t *bits, int W, int m, int n, int r0, int r1, int j, bool top, int need,
-                         int32_t *list)
+// Walk order: cell g of one side is layer k = floor(sqrt(g)) (the vertex
+// r0-1-k above the band, r1+k below it), index i = g - k*k in the layer:
+// i = 0 is column j itself, i = 2d-1 column j-d, i = 2d column j+d, on row
+// r0-1-k+d above the band or r1+k-d below it. Ascending g is the order in
+// which the optimal window takes tokens (nearest vertex first, then the
+// nearer column, left before right).
+__device__ __forceinline__ void walk_cell(int g, int j, int r0, int r1, bool top, int *row, int *col)
+{
+    const int k = isqrt_floor(g);
+    const int i = g - k * k;
+    const int d = (i + 1) >> 1;
+    *col = d == 0 ? j : ((i & 1) ? j - d : j + d);
+    *row = top ? r0 - 1 - k + d : r1 + k - d;
+}
+
+// Walks cells g in [g, gEnd) in order (one warp), appending the tokens found
+// to list[got ..] until `need` are held. Returns the tokens held; *gNext is
+// the first cell not examined.
+__device__ int walk_range(const uint32_t *bits, int W, int m, int n, int r0, int r1, int j, bool top, int need,
+                          int g, int gEnd, int maxIter, int got, int32_t *list, int *gNext)
 {
     const int lane = threadIdx.x & 31;
-    if (top ? r0 == 0 : r1 == m) return 0;
-    const int dmax = max(j, n - 1 - j);
-    const int kmax = top ? r0 - 1 + dmax : m - 1 - r1 + dmax;   // no cell beyond this layer
-    int got = 0;
-    for (int base = 0; got < need && isqrt_floor(base) <= kmax; base += 32) {
-        const int g = base + lane;
-        const int k = isqrt_floor(g);
-        const int i = g - k * k;
-        const int d = (i + 1) >> 1;
-        const int col = d == 0 ? j : ((i & 1) ? j - d : j + d);
-        const int row = top ? r0 - 1 - k + d : r1 + k - d;
+    for (int it = 0; got < need && g < gEnd && it < maxIter; ++it, g += 32) {
+        const int gl = g + lane;
+        int row, col;
+        walk_cell(gl, j, r0, r1, top, &row, &col);
         bool occ = false;
-        if (k <= kmax && col >= 0 && col < n && row >= 0 && row < m)
+        if (gl < gEnd && col >= 0 && col < n && row >= 0 && row < m && (top ? row < r0 : row >= r1))
             occ = (bits[(size_t)col * W + (row >> 5)] >> (row & 31)) & 1u;
         const unsigned bal = __ballot_sync(FULL, occ);
         const int rank = got + __popc(bal & ((1u << lane) - 1u));
         if (occ && rank < need) list[rank] = (row << 16) | col;
         got = min(need, got + __popc(bal));
     }
+    *gNext = g;
     return got;
+}
+
+// Tokens of one side in layers <= K (one warp): per column, a masked popcount
+// over the rows whose vertex is within K of the band.
+__device__ int side_count(const uint32_t *bits, int W, int m, int n, int r0, int r1, int j, bool top, int K)
+{
+    const int lane = threadIdx.x & 31;
+    int cnt = 0;
+    for (int c = lane; c < n; c += 32) {
+        const int d = iabs(c - j);
+        if (d > K) continue;
+        const int lo = top ? max(0, r0 - 1 - K + d) : r1;
+        const int hi = top ? r0 : min(m, r1 + K - d + 1);
+        for (int w = lo >> 5; w <= (hi - 1) >> 5; ++w) cnt += __popc(bits[(size_t)c * W + w] & row_mask(w, lo, hi));
+    }
+    return warp_sum(cnt);
+}
+
+// Sorts a[0..len) ascending (one warp, bitonic network over the next power
+// of two; the entries past len are padding and must fit in the buffer).
+__device__ void warp_sort_u32(uint32_t *a, int len)
+{
+    const int lane = threadIdx.x & 31;
+    if (len <= 1) return;
+    int P = 1;
+    while (P < len) P <<= 1;
+    for (int i = len + lane; i < P; i += 32) a[i] = 0xffffffffu;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = lane; i < P; i += 32) {
+                const int ij = i ^ jj;
+                if (ij > i) {
+                    const uint32_t x = a[i], y = a[ij];
+                    if ((x > y) == ((i & k) == 0)) { a[i] = y; a[ij] = x; }
+                }
+            }
+            __syncwarp();
+        }
+}
+
+// Collects, in walk order, the `need` nearest tokens of receiver j on one
+// side of the band, or all of them if fewer (one warp). While the
+// reservoirs near j are full the walk finds them in a few iterations. Once
+// they are depleted the walk would scan the empty area cell by cell, so
+// after a bounded walk the cut-off layer K (the first at which the count
+// reaches need) is found by binary search over per-column popcounts; the
+// tokens of the layers before K are gathered by their walk index and
+// sorted, and layer K alone is walked.
+__device__ int bird_side(const uint32_t *bits, int W, int m, int n, int r0, int r1, int j, bool top, int need,
+                         int32_t *list, int *s_cnt)
+{
+    const int lane = threadIdx.x & 31;
+    if (top ? r0 == 0 : r1 == m) return 0;
+    const int dmax = max(j, n - 1 - j);
+    const int kmax = top ? r0 - 1 + dmax : m - 1 - r1 + dmax;   // no cell beyond this layer
+    const int gAll = (kmax + 1) * (kmax + 1);
+    int gNext;
+    int got = walk_range(bits, W, m, n, r0, r1, j, top, need, 0, gAll, 8 + need / 8, 0, list, &gNext);
+    if (got >= need || gNext >= gAll) return got;
+    // layers below the walk's last one hold fewer than need tokens
+    int lo = isqrt_floor(gNext), hi = kmax;
+    if (side_count(bits, W, m, n, r0, r1, j, top, kmax) >= need) {
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (side_count(bits, W, m, n, r0, r1, j, top, mid) >= need) hi = mid; else lo = mid + 1;
+        }
+    } else {
+        lo = kmax;
+    }
+    const int K = lo;
+    const int before = K > 0 ? side_count(bits, W, m, n, r0, r1, j, top, K - 1) : 0;
+    // gather the walk indices of the tokens in layers < K, sort, decode
+    if (lane == 0) *s_cnt = 0;
+    __syncwarp();
+    uint32_t *keys = (uint32_t *)list;
+    for (int c = lane; c < n; c += 32) {
+        const int d = iabs(c - j);
+        if (d > K - 1) continue;
+        const int rlo = top ? max(0, r0 - 1 - (K - 1) + d) : r1;
+        const int rhi = top ? r0 : min(m, r1 + (K - 1) - d + 1);
+        const int i = d == 0 ? 0 : (c < j ? 2 * d - 1 : 2 * d);
+        for (int w = rlo >> 5; w <= (rhi - 1) >> 5; ++w) {
+            uint32_t x = bits[(size_t)c * W + w] & row_mask(w, rlo, rhi);
+            while (x) {
+                const int v = 32 * w + __ffs(x) - 1;
+                x &= x - 1;
+                const int k = (top ? r0 - 1 - v : v - r1) + d;
+                const int slot = atomicAdd(s_cnt, 1);
+                if (slot < before) keys[slot] = (uint32_t)(k * k + i);
+            }
+        }
+    }
+    __syncwarp();
+    warp_sort_u32(keys, before);
+    for (int t = lane; t < before; t += 32) {
+        int row, col;
+        walk_cell((int)keys[t], j, r0, r1, top, &row, &col);
+        list[t] = (row << 16) | col;
+    }
+    __syncwarp();
+    return walk_range(bits, W, m, n, r0, r1, j, top, need, K * K, (K + 1) * (K + 1), 0x7fffffff, before, list,
+                      &gNext);
 }
 
 __global__ void __launch_bounds__(64) k_bird(rr_instance *inst, JobWS *wsv, int count, int max_side)
 {
     extern __shared__ uint32_t birdsm[];
-    __shared__ int s_nt, s_nb, s_a, s_base, s_bad;
+    __shared__ int s_nt, s_nb, s_a, s_base, s_bad, s_cnt[2];
     const int q = blockIdx.x;
     if (q >= count) return;
     rr_instance *I = &inst[q];
@@ -79,8 +190,10 @@ __global__ void __launch_bounds__(64) k_bird(rr_instance *inst, JobWS *wsv, int 
     const int r0 = I->rect.r0, r1 = I->rect.r1, c0 = I->rect.c0, c1 = I->rect.c1, h = r1 - r0;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     uint32_t *bits = birdsm;                                               // n * W words
+    int listCap = 1;                                                      // next power of two >= max_side
+    while (listCap < max_side) listCap <<= 1;
     int32_t *topTok = (int32_t *)(birdsm + (size_t)max_side * ((max_side + 31) >> 5));
-    int32_t *botTok = topTok + max_side;
+    int32_t *botTok = topTok + listCap;
 
     // Feasibility (total surplus, Sec. III.C) and the offsets of the column
     // units, in column order.
@@ -134,7 +247,8 @@ __global__ void __launch_bounds__(64) k_bird(rr_instance *inst, JobWS *wsv, int 
         const int M = Rj.nband, need = h - M, nh = h - M;
         const int16_t *hr = ws.holeRows + (size_t)(j - c0) * h;
         if (wid < 2) {
-            const int got = bird_walk(bits, W, m, n, r0, r1, j, wid == 0, need, wid == 0 ? topTok : botTok);
+            const int got = bird_side(bits, W, m, n, r0, r1, j, wid == 0, need, wid == 0 ? topTok : botTok,
+                                      &s_cnt[wid]);
             if (lane == 0) { if (wid == 0) s_nt = got; else s_nb = got; }
         }
         __syncthreads();

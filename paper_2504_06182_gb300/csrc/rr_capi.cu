@@ -296,10 +296,13 @@ static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v
 static int budget(const rr_ctx *ctx, int base) { return ctx->shift >= 0 ? base << ctx->shift : base >> -ctx->shift; }
 
 // Shared memory of a k_bird block: reservoir-row bits of the largest grid
-// (column-major, one word per 32 rows) and the two walk lists.
+// (column-major, one word per 32 rows) and the two token lists (each the
+// next power of two >= max_side: they double as sort buffers).
 static size_t bird_smem_bytes(int max_side)
 {
-    return 4 * ((size_t)max_side * ((max_side + 31) / 32) + 2 * (size_t)max_side);
+    size_t cap = 1;
+    while (cap < (size_t)max_side) cap <<= 1;
+    return 4 * ((size_t)max_side * ((max_side + 31) / 32) + 2 * cap);
 }
 
 // Planning kernels over `count` device descriptors whose sides are <= max_side:

@@ -90,10 +90,12 @@ def test_bird_grid_256(planner, seed):
     assert ref.status == 0
 
 
-@pytest.mark.parametrize("n_tx", [32, 64, 128])
+@pytest.mark.parametrize("n_tx", [32, 64, 128, 256])
 def test_bird_paper_geometry(planner, n_tx):
     """The paper's runtime geometry (full-width target of n_tx rows in
-    ceil(n_tx / 0.6) rows): a feasible and an infeasible instance."""
+    ceil(n_tx / 0.6) rows): a feasible and an infeasible instance. Atoms
+    barely outnumber targets here, so the last columns find their tokens far
+    away in nearly empty reservoirs (the kernel's counting search)."""
     from paper_2504_06182_gb300 import RR_BITS32, RR_U8
     seen = set()
     for g in range(40):
@@ -176,8 +178,46 @@ def test_bird_grid_1024_replay(planner):
     st2, rmv = planner.plan(g, inst.rect, layout=RR_BITS32, n=1024)
     assert st == st2 == 0
     mv, rmv = mv.cpu().numpy(), rmv.cpu().numpy()
-    ncol = int(np.argmax(rmv[:, 1] != rmv[:, 3])) if (rmv[:, 1] != rmv[:, 3]).any() else len(rmv)
-    ncol = min(ncol, int(np.argmax(mv[:, 1] != mv[:, 3])))
+    # the column phase: every move before the first one into a receiver
+    # (a target column with fewer atoms than target rows)
+    r0, c0, r1, c1 = inst.rect
+    recv = np.zeros(1024, dtype=bool)
+    recv[c0:c1] = inst.grid[:, c0:c1].sum(axis=0) < r1 - r0
+    ncol = int(np.argmax(recv[mv[:, 3]]))
+    assert ncol > 0 and ncol == int(np.argmax(recv[rmv[:, 3]]))
     assert (mv[:ncol] == rmv[:ncol]).all()
     final = replay_moves(inst.grid, inst.rect, mv)
     assert_target_full(final, inst.rect, inst.grid)
+
+
+def test_bird_served():
+    """Served requests with RR_BIRD (waves of at most 5, three streams):
+    every result equals the oracle's bird plan and its batches."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2504_06182_gb300 as rr
+    from paper_2504_06182_gb300.planner import device_view
+    insts = gridgen.mixed_instances(78, 24, sides=tuple(range(32, 161, 32)), p_lo=0.55, p_hi=0.7)
+    srv = rr.rr_serve_open(max_side=256, slots=10, streams=3, max_wave=5, flags=rr.RR_WITH_BATCH | rr.RR_BIRD,
+                           arena_bytes=1 << 30, heap_bytes=1 << 30)
+    try:
+        tickets = []
+        for inst in insts:
+            m, n = inst.grid.shape
+            st, t = rr.rr_serve_submit(srv, np.ascontiguousarray(inst.grid), rr.RR_U8, m, n, inst.rect)
+            assert st == rr.RR_OK
+            tickets.append(t)
+        for inst, t in zip(insts, tickets):
+            st, res = rr.rr_serve_poll(srv, t, timeout_us=120_000_000)
+            assert st == rr.RR_OK, st
+            ref = oracle.bird(inst.grid, inst.rect)
+            assert res.status == ref.status and res.n_moves == len(ref.moves)
+            if ref.status == 0:
+                assert (device_view(res.d_moves, (res.n_moves, 4)).cpu().numpy() == ref.moves).all()
+                rops, rmem = oracle.batch(ref.moves, *inst.grid.shape)
+                assert res.n_ops == len(rops) and res.n_members == len(rmem)
+                assert (device_view(res.d_ops, (res.n_ops, 3)).cpu().numpy() == rops).all()
+                assert (device_view(res.d_members, (res.n_members,)).cpu().numpy() == rmem).all()
+            assert rr.rr_serve_release(srv, t) == rr.RR_OK
+    finally:
+        rr.rr_serve_close(srv)
