@@ -159,14 +159,15 @@ __global__ void k_bsetup(rr_instance *inst, JobWS *wsv, int count, Arena A)
 // ---------------------------------------------------------------- Gamma
 // Vertex (r, c) is covered by the vertical parts of the moves ending in
 // column c (the corner of an L-move included) and by the horizontal parts of
-// the L-moves running along row r (their destination column excluded). When
-// every move of the first kind precedes every move of the second kind at
-// each vertex -- always so for red-rec plans, since a corridor only crosses
-// a column after that column's moves were emitted -- the next path through a
-// vertex follows from two sweeps in id order: one per column over the moves
-// ending there, one per row over the L-moves on it. The column sweep checks
-// that order at every vertex; an instance that breaks it falls back to
-// per-vertex path lists.
+// the L-moves running along row r (their destination column excluded). Two
+// sweeps in id order -- one per row over the L-moves on it, one per column
+// over the moves ending there -- give each vertex's horizontal and vertical
+// coverers as two id-ordered chains. In red-rec plans every vertical
+// coverer precedes every horizontal one (a corridor only crosses a column
+// after that column's moves were emitted), so the chains are concatenated;
+// elsewhere (bird's corridors cross columns solved later) the column sweep
+// merges the two chains of that vertex by id. Per-vertex path lists remain
+// as the fallback for a chain too long to merge.
 
 __global__ void k_gcount(rr_instance *inst, JobWS *wsv, int count)
 {
@@ -323,10 +324,15 @@ __global__ void k_gsweep_h(rr_instance *inst, JobWS *wsv, int count, int lineCap
     }
 }
 
+// Longest coverer chain one lane merges at a vertex; an instance with a longer
+// one takes the per-vertex fallback.
+constexpr int MERGE_LIMIT = 1 << 16;
+
 // Column sweep: the moves ending in each column in id order; consecutive
 // vertical coverers are linked, the last one to the vertex's first
-// horizontal coverer. Flags the instance if a horizontal coverer precedes a
-// vertical one anywhere.
+// horizontal coverer. Where a horizontal coverer precedes a vertical one (a
+// bird corridor through a column solved later), the two id-ordered chains of
+// that vertex are merged by id instead.
 __global__ void k_gsweep_v(rr_instance *inst, JobWS *wsv, int count, int lineCap)
 {
     extern __shared__ int32_t sweepbuf[];
@@ -337,8 +343,9 @@ __global__ void k_gsweep_v(rr_instance *inst, JobWS *wsv, int count, int lineCap
     JobWS &ws = wsv[q];
     const int lane = threadIdx.x & 31;
     const int n = I->n, m = I->m;
-    int32_t *lastPos = sweepbuf + (threadIdx.x >> 5) * 2 * lineCap;
+    int32_t *lastPos = sweepbuf + (threadIdx.x >> 5) * 3 * lineCap;
     int32_t *lastId = lastPos + lineCap;
+    int32_t *firstId = lastId + lineCap;
     for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n; c += gridDim.x * (blockDim.x >> 5)) {
         for (int r = lane; r < m; r += 32) lastPos[r] = -1;
         __syncwarp();
@@ -352,6 +359,7 @@ __global__ void k_gsweep_v(rr_instance *inst, JobWS *wsv, int count, int lineCap
                 const int r = p.src_row + t * step;
                 const int prev = lastPos[r];
                 if (prev >= 0) ws.nextAt[prev] = b;
+                else firstId[r] = b;
                 lastPos[r] = base + t;
                 lastId[r] = b;
             }
@@ -361,8 +369,26 @@ __global__ void k_gsweep_v(rr_instance *inst, JobWS *wsv, int count, int lineCap
         for (int r = lane; r < m; r += 32) {
             if (lastPos[r] < 0) continue;
             const int f = ws.firstH[(size_t)r * n + c];
-            bad |= f >= 0 && f < lastId[r];
-            ws.nextAt[lastPos[r]] = f;
+            if (f < 0 || f > lastId[r]) {              // every vertical coverer first
+                ws.nextAt[lastPos[r]] = f;
+                continue;
+            }
+            // merge: take the smaller id of the two chain heads, link it
+            // after the previous one, advance its chain
+            int v = firstId[r], h = f, prevEntry = -1, steps = 0;
+            for (; (v >= 0 || h >= 0) && steps < MERGE_LIMIT; ++steps) {
+                const bool takeV = h < 0 || (v >= 0 && v < h);
+                const int x = takeV ? v : h;
+                const rr_move p = I->moves[x];
+                const int e = ws.pairOff[x] + (takeV ? iabs(p.dst_col - p.src_col) + iabs(r - p.src_row)
+                                                     : iabs(c - p.src_col));
+                const int nx = (takeV && e == lastPos[r]) ? -1 : ws.nextAt[e];
+                if (prevEntry >= 0) ws.nextAt[prevEntry] = x;
+                prevEntry = e;
+                if (takeV) v = nx; else h = nx;
+            }
+            if (prevEntry >= 0) ws.nextAt[prevEntry] = -1;
+            bad |= steps >= MERGE_LIMIT;
         }
         if (__any_sync(FULL, bad) && lane == 0) ws.genericGamma = 1;
         __syncwarp();

@@ -374,14 +374,14 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, 
         int P2 = 32;
         while (P2 < max_side) P2 <<= 1;
         if (8 * 4 * P2 > ctx->smemLimit[SM_GSORT] || 8 * 4 * max_side > ctx->smemLimit[SM_GSWEEP_H] ||
-            8 * 8 * max_side > ctx->smemLimit[SM_GSWEEP_V])
+            8 * 12 * max_side > ctx->smemLimit[SM_GSWEEP_V])
             return fail(ctx, RR_ERR_ARG, "Gamma sweeps: shared memory for side %d too large", max_side);
         mark(ctx, s, "k_gsort");
         k_gsort<<<dim3(lineBlocks, count), 256, 8 * 4 * (size_t)P2, s>>>(d_inst, ws, count, P2);
         mark(ctx, s, "k_gsweep_h");
         k_gsweep_h<<<dim3(lineBlocks, count), 256, 8 * 4 * (size_t)max_side, s>>>(d_inst, ws, count, max_side);
         mark(ctx, s, "k_gsweep_v");
-        k_gsweep_v<<<dim3(lineBlocks, count), 256, 8 * 8 * (size_t)max_side, s>>>(d_inst, ws, count, max_side);
+        k_gsweep_v<<<dim3(lineBlocks, count), 256, 8 * 12 * (size_t)max_side, s>>>(d_inst, ws, count, max_side);
         mark(ctx, s, "k_galloc");
         k_galloc<<<count, 256, 0, s>>>(d_inst, ws, count, A);
     }
