@@ -89,6 +89,21 @@ int rr_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect r
 int rr_bird_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect,
                  rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream);
 
+/* rr_plan / rr_bird_plan with explicit planning flags: RR_BIRD selects the
+ * bird algorithm; RR_STRICT_RESERVOIR selects the strict reading of target
+ * sub-rectangles. By default (the reading this library uses elsewhere) a
+ * column outside [c0, c1) with at least m - (r1 - r0) atoms is first solved
+ * on its own with its reservoir traps (rows outside [r0, r1)) as targets, so
+ * that its band-row atoms become donatable; with RR_STRICT_RESERVOIR such
+ * columns stay as they are and donate only the atoms already in their
+ * reservoir rows (Sec. III.C: donors give reservoir atoms only), so every
+ * atom moves at most once, at the price of feasibility (most centred square
+ * targets of 0.7 times the side at fill 0.6 become infeasible). With c0 = 0
+ * and c1 = n both readings are the paper's algorithm. Other arguments and
+ * behaviour as rr_plan; unknown flags give RR_ERR_ARG. */
+int rr_plan_mode(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect, int flags,
+                 rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream);
+
 /* Batch a move list (Alg. 4 + Sec. IV): dependencies = every earlier move
  * whose path shares a vertex; ready moves are visited in ascending id and a
  * move's next step joins the batch iff it has the first member's direction and
@@ -112,6 +127,7 @@ int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, int m, int n,
 #define RR_BATCH_ONLY 2   /* skip planning: instances carry moves and n_moves (status RR_OK) */
 #define RR_GRAPH 4        /* replay a captured CUDA graph of the launch sequence (below) */
 #define RR_BIRD 8         /* plan with the bird algorithm (as rr_bird_plan) instead of red-rec */
+#define RR_STRICT_RESERVOIR 16  /* strict reading of target sub-rectangles (rr_plan_mode) */
 typedef struct {
     const void *grid;
     int32_t layout, m, n, pad0;
@@ -195,7 +211,8 @@ typedef struct {
     int32_t slots;           /* requests admitted and not yet released, at most */
     int32_t streams;         /* waves in flight at once */
     int32_t max_wave;        /* requests per wave, <= slots */
-    int32_t flags;           /* RR_WITH_BATCH to also batch every plan; RR_BIRD to plan with bird */
+    int32_t flags;           /* RR_WITH_BATCH to also batch every plan; RR_BIRD to plan with bird;
+                                RR_STRICT_RESERVOIR as in rr_plan_mode */
     int32_t pad;
     int64_t arena_bytes;     /* workspace arena per stream */
     int64_t heap_bytes;      /* device heap for batch results (16 B per elementary step) */

@@ -43,10 +43,10 @@ def lib():
         L.rro_window.restype = i32
         L.rro_split.argtypes = [P, i32, P, i32, P, i32, i32, i32, i32, P]
         L.rro_split.restype = i32
-        L.rro_plan.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, i64, P]
-        L.rro_plan.restype = i32
-        L.rro_bird.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, i64, P]
-        L.rro_bird.restype = i32
+        L.rro_plan_mode.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, i64, P, i32]
+        L.rro_plan_mode.restype = i32
+        L.rro_bird_mode.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, i64, P, i32]
+        L.rro_bird_mode.restype = i32
         L.rro_batch.argtypes = [P, i64, i32, i32, P, i64, P, i64, P, P]
         L.rro_batch.restype = i32
         L.rro_batch_prefix.argtypes = [P, i64, i32, i32, i64, P, i64, P, i64, P, P]
@@ -83,7 +83,9 @@ class Plan:
         self.events = events        # (e, 5) int32: case, donor, receiver, x, a
 
 
-def plan(grid: np.ndarray, rect, with_trace: bool = False) -> Plan:
+def plan(grid: np.ndarray, rect, with_trace: bool = False, strict: bool = False) -> Plan:
+    """red-rec (Alg. 1). strict: the strict-reservoir reading of target
+    sub-rectangles (outer columns donate reservoir-row atoms only)."""
     grid = np.ascontiguousarray(grid, dtype=np.uint8)
     m, n = grid.shape
     r0, c0, r1, c1 = (int(v) for v in rect)
@@ -95,9 +97,9 @@ def plan(grid: np.ndarray, rect, with_trace: bool = False) -> Plan:
     events = np.zeros((max(cap_ev, 1), 5), dtype=np.int32)
     while True:
         moves = np.zeros((max(cap, 1), 4), dtype=np.int32)
-        st = lib().rro_plan(_ptr(grid), m, n, r0, c0, r1, c1, _ptr(moves), cap,
-                            ctypes.byref(nm), _ptr(sigma), _ptr(events) if with_trace else None,
-                            cap_ev, ctypes.byref(ne))
+        st = lib().rro_plan_mode(_ptr(grid), m, n, r0, c0, r1, c1, _ptr(moves), cap,
+                                 ctypes.byref(nm), _ptr(sigma), _ptr(events) if with_trace else None,
+                                 cap_ev, ctypes.byref(ne), int(strict))
         if st == ERR_CAPACITY:
             cap = nm.value
             continue
@@ -108,10 +110,10 @@ def plan(grid: np.ndarray, rect, with_trace: bool = False) -> Plan:
                 events[: ne.value].copy() if with_trace else None)
 
 
-def bird(grid: np.ndarray, rect, with_trace: bool = False) -> Plan:
+def bird(grid: np.ndarray, rect, with_trace: bool = False, strict: bool = False) -> Plan:
     """The bird planner (Alg. 2, Sec. III.E). With with_trace, events holds
     one row per receiver: (column, tokens from above the band, tokens from
-    below it); sigma is not filled."""
+    below it); sigma is not filled. strict as in plan()."""
     grid = np.ascontiguousarray(grid, dtype=np.uint8)
     m, n = grid.shape
     r0, c0, r1, c1 = (int(v) for v in rect)
@@ -122,8 +124,8 @@ def bird(grid: np.ndarray, rect, with_trace: bool = False) -> Plan:
     units = np.zeros((max(cap_u, 1), 3), dtype=np.int32)
     while True:
         moves = np.zeros((max(cap, 1), 4), dtype=np.int32)
-        st = lib().rro_bird(_ptr(grid), m, n, r0, c0, r1, c1, _ptr(moves), cap, ctypes.byref(nm),
-                            _ptr(units) if with_trace else None, cap_u, ctypes.byref(nu))
+        st = lib().rro_bird_mode(_ptr(grid), m, n, r0, c0, r1, c1, _ptr(moves), cap, ctypes.byref(nm),
+                                 _ptr(units) if with_trace else None, cap_u, ctypes.byref(nu), int(strict))
         if st == ERR_CAPACITY:
             cap = nm.value
             continue

@@ -21,7 +21,9 @@
  *    its own reservoir cells as virtual targets, so that its band-row atoms
  *    are pushed out into its reservoir rows where they can be donated. With
  *    a full-width target there are no such columns and the method is the
- *    paper's.
+ *    paper's. The strict reading (mode `strict`) leaves every outer column
+ *    as it is: only its reservoir-row atoms are donatable, as the paper's
+ *    donors donate only reservoir atoms, and its band-row atoms never move.
  *  - Emission order inside one solve unit (Sec. III.A, "Generating moves"):
  *    paths that move toward larger row indices first, by descending target
  *    row, then paths toward smaller row indices by ascending target row, so
@@ -224,6 +226,15 @@ int rro_plan(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
              int32_t *sigma_out, int32_t *events, int64_t cap_ev,
              int64_t *n_events)
 {
+    return rro_plan_mode(grid, m, n, r0, c0, r1, c1, moves, cap, n_moves, sigma_out, events, cap_ev,
+                         n_events, 0);
+}
+
+int rro_plan_mode(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
+                  int32_t *moves, int64_t cap, int64_t *n_moves,
+                  int32_t *sigma_out, int32_t *events, int64_t cap_ev,
+                  int64_t *n_events, int strict)
+{
     if (!grid || !n_moves || m < 1 || n < 1 || r0 < 0 || r0 >= r1 || r1 > m ||
         c0 < 0 || c0 >= c1 || c1 > n || cap < 0 || (cap > 0 && !moves))
         return E_ARG;
@@ -271,7 +282,7 @@ int rro_plan(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
                 pool[c].row[pool[c].cnt] = s[k];
                 pool[c].live[pool[c].cnt++] = 1;
             }
-        } else if (K[c] >= R) {
+        } else if (!strict && K[c] >= R) {
             /* Virtual targets = the reservoir cells 0..r0-1 and r1..m-1. */
             const int nbot = m - r1;
             for (int k = 0; k < r0; ++k) unit[cnt++] = (mv_t){s[k], c, k, c};
@@ -464,6 +475,13 @@ int rro_bird(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
              int32_t *moves, int64_t cap, int64_t *n_moves,
              int32_t *units, int64_t cap_units, int64_t *n_units)
 {
+    return rro_bird_mode(grid, m, n, r0, c0, r1, c1, moves, cap, n_moves, units, cap_units, n_units, 0);
+}
+
+int rro_bird_mode(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
+                  int32_t *moves, int64_t cap, int64_t *n_moves,
+                  int32_t *units, int64_t cap_units, int64_t *n_units, int strict)
+{
     if (!grid || !n_moves || m < 1 || n < 1 || r0 < 0 || r0 >= r1 || r1 > m ||
         c0 < 0 || c0 >= c1 || c1 > n || cap < 0 || (cap > 0 && !moves))
         return E_ARG;
@@ -494,7 +512,7 @@ int rro_bird(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
             int w = rro_window(rows, K, r0, h);
             if (w < 0) { st = E_BUG; goto done; }
             for (int k = 0; k < h; ++k) unit[cnt++] = (mv_t){rows[w + k], c, r0 + k, c};
-        } else if (K >= R) {
+        } else if (!strict && K >= R) {
             const int nbot = m - r1;
             for (int k = 0; k < r0; ++k) unit[cnt++] = (mv_t){rows[k], c, k, c};
             for (int k = 0; k < nbot; ++k) unit[cnt++] = (mv_t){rows[K - nbot + k], c, r1 + k, c};

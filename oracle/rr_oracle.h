@@ -56,6 +56,17 @@ int rro_plan(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
              int32_t *sigma_out, int32_t *events, int64_t cap_ev,
              int64_t *n_events);
 
+/* rro_plan with a geometry mode: strict = 0 solves columns outside the
+ * target columns with their own reservoir cells as virtual targets (their
+ * band-row atoms become donatable); strict = 1 leaves them as they are, so
+ * only their reservoir-row atoms are donatable (the paper's donors donate
+ * reservoir atoms only, Sec. III.C). With a full-width target both are the
+ * paper's algorithm. */
+int rro_plan_mode(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
+                  int32_t *moves, int64_t cap, int64_t *n_moves,
+                  int32_t *sigma_out, int32_t *events, int64_t cap_ev,
+                  int64_t *n_events, int strict);
+
 /* The bird planner (Alg. 2, Sec. III.E): red-rec's column phase, then the
  * unsolved columns left to right, each filled through its generalised 1D
  * instance over every token of the grid. moves: cap*4 int32. units:
@@ -64,6 +75,11 @@ int rro_plan(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
 int rro_bird(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
              int32_t *moves, int64_t cap, int64_t *n_moves,
              int32_t *units, int64_t cap_units, int64_t *n_units);
+
+/* rro_bird with the geometry mode of rro_plan_mode. */
+int rro_bird_mode(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
+                  int32_t *moves, int64_t cap, int64_t *n_moves,
+                  int32_t *units, int64_t cap_units, int64_t *n_units, int strict);
 
 /* The batching routine (Alg. 4 with the local constraint set of Sec. IV).
  * ops: cap_ops*3 int32; members: cap_members int32. */

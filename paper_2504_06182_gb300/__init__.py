@@ -22,6 +22,7 @@ RR_WITH_BATCH = 1
 RR_BATCH_ONLY = 2
 RR_GRAPH = 4
 RR_BIRD = 8
+RR_STRICT_RESERVOIR = 16
 RR_MAX_SIDE = 1024
 STATUS_NAMES = {0: "OK", 1: "INFEASIBLE", -1: "ERR_ARG", -2: "ERR_CAPACITY", -3: "ERR_CUDA",
                 -4: "ERR_TIMEOUT", -5: "ERR_WORKSPACE", -6: "ERR_INTERNAL"}
@@ -65,7 +66,7 @@ class rr_serve_result(ctypes.Structure):
                 ("t_done_us", ctypes.c_double)]
 
 
-EXPORTS = ("rr_ctx_create", "rr_ctx_destroy", "rr_plan", "rr_bird_plan", "rr_batch", "rr_plan_batched", "rr_set_tracing",
+EXPORTS = ("rr_ctx_create", "rr_ctx_destroy", "rr_plan", "rr_bird_plan", "rr_plan_mode", "rr_batch", "rr_plan_batched", "rr_set_tracing",
            "rr_stage_times", "rr_launch_count", "rr_autotune", "rr_set_config", "rr_last_error", "rr_plan_noalloc", "rr_serve_open", "rr_serve_submit",
            "rr_serve_poll", "rr_serve_release", "rr_serve_close")
 RR_NOALLOC_MAX_SIDE = 256
@@ -90,6 +91,8 @@ def load(path: str = LIB_PATH):
     L.rr_plan.restype = I32
     L.rr_bird_plan.argtypes = [P, P, I32, I32, I32, rr_rect, P, I64, ctypes.POINTER(I64), P]
     L.rr_bird_plan.restype = I32
+    L.rr_plan_mode.argtypes = [P, P, I32, I32, I32, rr_rect, I32, P, I64, ctypes.POINTER(I64), P]
+    L.rr_plan_mode.restype = I32
     L.rr_batch.argtypes = [P, P, I64, I32, I32, P, I64, P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64), P]
     L.rr_batch.restype = I32
     L.rr_plan_batched.argtypes = [P, P, I32, I32, I32, P]
@@ -178,6 +181,14 @@ def rr_bird_plan(ctx, d_grid, layout, m, n, rect, d_moves, cap, stream=None):
     nm = ctypes.c_int64(0)
     st = load().rr_bird_plan(ctx, _addr(d_grid), int(layout), int(m), int(n), rr_rect(*[int(v) for v in rect]),
                              _addr(d_moves), int(cap), ctypes.byref(nm), _stream(stream))
+    return st, nm.value
+
+
+def rr_plan_mode(ctx, d_grid, layout, m, n, rect, flags, d_moves, cap, stream=None):
+    """Planning with flags RR_BIRD / RR_STRICT_RESERVOIR. Returns (status, n_moves)."""
+    nm = ctypes.c_int64(0)
+    st = load().rr_plan_mode(ctx, _addr(d_grid), int(layout), int(m), int(n), rr_rect(*[int(v) for v in rect]),
+                             int(flags), _addr(d_moves), int(cap), ctypes.byref(nm), _stream(stream))
     return st, nm.value
 
 

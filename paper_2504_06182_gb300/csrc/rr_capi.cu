@@ -10,7 +10,7 @@
 namespace rrk {
 __global__ void k_plan_setup(rr_instance *, JobWS *, int, int, Arena);
 __global__ void k_transpose(rr_instance *, JobWS *, int);
-__global__ void k_colstats(rr_instance *, JobWS *, int);
+__global__ void k_colstats(rr_instance *, JobWS *, int, int);
 __global__ void k_pair(rr_instance *, JobWS *, int);
 __global__ void k_emit_cols(rr_instance *, JobWS *, int);
 __global__ void k_emit_recv(rr_instance *, JobWS *, int);
@@ -306,11 +306,14 @@ static size_t bird_smem_bytes(int max_side)
 }
 
 // Planning kernels over `count` device descriptors whose sides are <= max_side:
-// red-rec (Alg. 1), or with `bird` the bird algorithm (Alg. 2), which shares
-// red-rec's column phase.
+// red-rec (Alg. 1), or with RR_BIRD the bird algorithm (Alg. 2), which shares
+// red-rec's column phase; RR_STRICT_RESERVOIR selects the strict reading of
+// target sub-rectangles for either.
 static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, int max_side, cudaStream_t s,
-                       bool bird)
+                       int flags)
 {
+    const bool bird = (flags & RR_BIRD) != 0;
+    const int strict = (flags & RR_STRICT_RESERVOIR) ? 1 : 0;
     const Arena A = arena_of(ctx);
     const int colBlocks = clampi(std::max(1, budget(ctx, 4096) / count), 1, (max_side + 7) / 8);
     const int tiles = ((max_side + 31) / 32) * ((max_side + 31) / 32);
@@ -321,7 +324,7 @@ static int launch_plan(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, i
     mark(ctx, s, "k_transpose");
     k_transpose<<<dim3(trBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_colstats");
-    k_colstats<<<dim3(colBlocks, count), 256, 0, s>>>(d_inst, ws, count);
+    k_colstats<<<dim3(colBlocks, count), 256, 0, s>>>(d_inst, ws, count, strict);
     if (bird) {
         const size_t birdSmem = bird_smem_bytes(max_side);
         if (birdSmem > (size_t)ctx->smemLimit[SM_BIRD])
@@ -460,13 +463,12 @@ static bool rect_ok(int m, int n, rr_rect R)
 }
 
 static int plan_one(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect, rr_move *d_moves,
-                    int64_t cap, int64_t *n_moves, cudaStream_t stream, bool bird)
+                    int64_t cap, int64_t *n_moves, cudaStream_t stream, int flags, const char *name)
 {
-    const char *name = bird ? "rr_bird_plan" : "rr_plan";
     if (!ctx || !d_grid || !n_moves || (layout != RR_U8 && layout != RR_BITS32) || !rect_ok(m, n, rect) ||
-        cap < 0 || (cap > 0 && !d_moves))
-        return fail(ctx, RR_ERR_ARG, "%s: bad argument (m=%d n=%d rect=[%d,%d,%d,%d] layout=%d cap=%lld)", name, m,
-                    n, rect.r0, rect.c0, rect.r1, rect.c1, layout, (long long)cap);
+        cap < 0 || (cap > 0 && !d_moves) || (flags & ~(RR_BIRD | RR_STRICT_RESERVOIR)))
+        return fail(ctx, RR_ERR_ARG, "%s: bad argument (m=%d n=%d rect=[%d,%d,%d,%d] layout=%d cap=%lld flags=%d)",
+                    name, m, n, rect.r0, rect.c0, rect.r1, rect.c1, layout, (long long)cap, flags);
     rr_instance h;
     std::memset(&h, 0, sizeof(h));
     h.grid = d_grid; h.layout = layout; h.m = m; h.n = n; h.rect = rect;
@@ -474,7 +476,7 @@ static int plan_one(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, r
     ctx->nmarks = 0;
     CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->d_one, &h, sizeof(h), cudaMemcpyHostToDevice, stream));
-    int st = launch_plan(ctx, ctx->d_one, ctx->d_ws, 1, std::max(m, n), stream, bird);
+    int st = launch_plan(ctx, ctx->d_one, ctx->d_ws, 1, std::max(m, n), stream, flags);
     if (st != RR_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(&h, ctx->d_one, sizeof(h), cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaStreamSynchronize(stream));
@@ -487,13 +489,19 @@ static int plan_one(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, r
 extern "C" int rr_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect,
                        rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream)
 {
-    return plan_one(ctx, d_grid, layout, m, n, rect, d_moves, cap, n_moves, stream, false);
+    return plan_one(ctx, d_grid, layout, m, n, rect, d_moves, cap, n_moves, stream, 0, "rr_plan");
 }
 
 extern "C" int rr_bird_plan(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect,
                             rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream)
 {
-    return plan_one(ctx, d_grid, layout, m, n, rect, d_moves, cap, n_moves, stream, true);
+    return plan_one(ctx, d_grid, layout, m, n, rect, d_moves, cap, n_moves, stream, RR_BIRD, "rr_bird_plan");
+}
+
+extern "C" int rr_plan_mode(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect, int flags,
+                            rr_move *d_moves, int64_t cap, int64_t *n_moves, cudaStream_t stream)
+{
+    return plan_one(ctx, d_grid, layout, m, n, rect, d_moves, cap, n_moves, stream, flags, "rr_plan_mode");
 }
 
 extern "C" int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, int m, int n, rr_op *d_ops,
@@ -552,10 +560,10 @@ static int launch_sequence(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
 {
     CUDA_TRY(cudaMemsetAsync(ctx->d_top, 0, sizeof(unsigned long long), stream));
     const bool plan = !(flags & RR_BATCH_ONLY), batch = (flags & (RR_WITH_BATCH | RR_BATCH_ONLY)) != 0;
-    const bool bird = (flags & RR_BIRD) != 0;
+    const int pflags = flags & (RR_BIRD | RR_STRICT_RESERVOIR);
     const int *frac = PIPE_FRAC64[ctx->pipe > 0 && ctx->pipe < PIPE_SPLITS ? ctx->pipe : 0];
     if (!batch || frac[0] == 0 || count < PIPE_MIN) {
-        int st = plan ? launch_plan(ctx, d_inst, ctx->d_ws, count, max_side, stream, bird) : RR_OK;
+        int st = plan ? launch_plan(ctx, d_inst, ctx->d_ws, count, max_side, stream, pflags) : RR_OK;
         if (st == RR_OK && batch)
             st = launch_batch(ctx, d_inst, ctx->d_ws, count, max_side, stream, SIM_CLASSES, nullptr, nullptr);
         return st;
@@ -573,7 +581,7 @@ static int launch_sequence(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
         cudaStream_t gs = ctx->leadStream[g];
         CUDA_TRY(cudaStreamWaitEvent(gs, ctx->evStart, 0));
         ctx->quiet = g > 0;                  // stage marks follow the first group
-        if (plan) st = launch_plan(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, hi - lo, max_side, gs, bird);
+        if (plan) st = launch_plan(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, hi - lo, max_side, gs, pflags);
         if (st == RR_OK)
             st = launch_batch(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, hi - lo, max_side, gs, SIM_ONE, prevSim,
                               ctx->evSim[g]);
@@ -589,7 +597,7 @@ static int launch_sequence(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
     if (st == RR_OK) {
         cudaStream_t rs = ctx->restStream;
         CUDA_TRY(cudaStreamWaitEvent(rs, ctx->evStart, 0));
-        if (plan) st = launch_plan(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, count - lo, max_side, rs, bird);
+        if (plan) st = launch_plan(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, count - lo, max_side, rs, pflags);
         if (st == RR_OK)
             st = launch_batch(ctx, ctx->d_pinst + lo, ctx->d_ws + lo, count - lo, max_side, rs, SIM_CLASSES, prevSim,
                               nullptr);
@@ -611,7 +619,7 @@ extern "C" int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int 
                                cudaStream_t stream)
 {
     if (!ctx || !d_inst || count < 1 || count > 65535 || max_side < 1 || max_side > RR_MAX_SIDE ||
-        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY | RR_GRAPH | RR_BIRD)))
+        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY | RR_GRAPH | RR_BIRD | RR_STRICT_RESERVOIR)))
         return fail(ctx, RR_ERR_ARG, "rr_plan_batched: bad argument (count=%d max_side=%d flags=%d)", count,
                     max_side, flags);
     int st = ensure_ws(ctx, count);
@@ -658,7 +666,7 @@ extern "C" int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
                            cudaStream_t stream, int32_t *nclass, int32_t *shift, int32_t *pipe)
 {
     if (!ctx || !d_inst || count < 1 || count > 65535 || max_side < 1 || max_side > RR_MAX_SIDE ||
-        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY | RR_BIRD)))
+        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY | RR_BIRD | RR_STRICT_RESERVOIR)))
         return fail(ctx, RR_ERR_ARG, "rr_autotune: bad argument (count=%d max_side=%d flags=%d)", count, max_side,
                     flags);
     int st = ensure_ws(ctx, count);

@@ -15,7 +15,7 @@
 namespace rrk {
 __global__ void k_plan_setup(rr_instance *, JobWS *, int, int, Arena);
 __global__ void k_transpose(rr_instance *, JobWS *, int);
-__global__ void k_colstats(rr_instance *, JobWS *, int);
+__global__ void k_colstats(rr_instance *, JobWS *, int, int);
 __global__ void k_pair(rr_instance *, JobWS *, int);
 __global__ void k_emit_cols(rr_instance *, JobWS *, int);
 __global__ void k_emit_recv(rr_instance *, JobWS *, int);
@@ -80,7 +80,7 @@ extern "C" int rr_plan_noalloc(const void *d_grid, int layout, int m, int n, rr_
     const int trBlocks = (tiles + 7) / 8;
     k_plan_setup<<<1, 128, 0, stream>>>(d_inst, d_ws, 1, side, A);
     k_transpose<<<dim3(trBlocks, 1), 256, 0, stream>>>(d_inst, d_ws, 1);
-    k_colstats<<<dim3(colBlocks, 1), 256, 0, stream>>>(d_inst, d_ws, 1);
+    k_colstats<<<dim3(colBlocks, 1), 256, 0, stream>>>(d_inst, d_ws, 1, 0);
     k_pair<<<1, 32, (size_t)side * 30 + 64, stream>>>(d_inst, d_ws, 1);
     k_emit_cols<<<dim3(colBlocks, 1), 256, 0, stream>>>(d_inst, d_ws, 1);
     k_emit_recv<<<dim3(side, 1), 256, 0, stream>>>(d_inst, d_ws, 1);

@@ -95,8 +95,11 @@ __global__ void k_transpose(rr_instance *inst, JobWS *wsv, int count)
 // One warp per column. Target columns of non-negative surplus get the exact
 // 1D solve: the h sources are the band atoms plus the a nearest atoms above
 // and the x-a nearest below (a contiguous window of the sorted sources),
-// a chosen by minimum total distance with the largest a on ties.
-__global__ void k_colstats(rr_instance *inst, JobWS *wsv, int count)
+// a chosen by minimum total distance with the largest a on ties. Columns
+// outside the target columns are pushed into their reservoir rows when they
+// have the atoms for it, unless `strict` (then only their reservoir-row atoms
+// are donatable and nothing in them moves).
+__global__ void k_colstats(rr_instance *inst, JobWS *wsv, int count, int strict)
 {
     const int q = blockIdx.y;
     if (q >= count) return;
@@ -162,7 +165,7 @@ __global__ void k_colstats(rr_instance *inst, JobWS *wsv, int count)
                 ci.kind = KIND_RECEIVER;
                 ci.ptop = 0; ci.pbot = 0;
             }
-        } else if (K >= R) {
+        } else if (!strict && K >= R) {
             // Virtual targets = this column's reservoir cells: the first r0
             // atoms go to rows 0..r0-1, the last m-r1 to rows r1..m-1.
             ci.kind = KIND_OUTER_FULL;

@@ -231,7 +231,8 @@ static bool pump(rr_server *S)
         if (!cnt) break;                                         // the head of the queue does not fit yet
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(S->dDesc[s], S->hDesc[s], sizeof(rr_instance) * cnt, cudaMemcpyHostToDevice, st);
-        int r = e == cudaSuccess ? rr_plan_batched(S->ctx[s], S->dDesc[s], cnt, S->cfg.max_side, S->cfg.flags & RR_BIRD, st) : RR_ERR_CUDA;
+        int r = e == cudaSuccess ? rr_plan_batched(S->ctx[s], S->dDesc[s], cnt, S->cfg.max_side,
+                                                        S->cfg.flags & (RR_BIRD | RR_STRICT_RESERVOIR), st) : RR_ERR_CUDA;
         if (r == RR_OK) e = cudaMemcpyAsync(S->hDesc[s], S->dDesc[s], sizeof(rr_instance) * cnt, cudaMemcpyDeviceToHost, st);
         if (r == RR_OK && e == cudaSuccess) e = cudaEventRecord(W.ev, st);
         if (r != RR_OK || e != cudaSuccess) { fail_all(S, r != RR_OK ? r : RR_ERR_CUDA); return true; }
@@ -276,7 +277,7 @@ extern "C" int rr_serve_open(rr_server **out, const rr_serve_config *cfg)
 {
     if (!out || !cfg || cfg->max_side < 1 || cfg->max_side > RR_MAX_SIDE || cfg->slots < 1 || cfg->streams < 1 ||
         cfg->streams > 64 || cfg->max_wave < 1 || cfg->max_wave > cfg->slots || cfg->max_wave > 65535 ||
-        (cfg->flags & ~(RR_WITH_BATCH | RR_BIRD)) || cfg->heap_bytes < 0 || cfg->input_bytes < 0)
+        (cfg->flags & ~(RR_WITH_BATCH | RR_BIRD | RR_STRICT_RESERVOIR)) || cfg->heap_bytes < 0 || cfg->input_bytes < 0)
         return RR_ERR_ARG;
     *out = nullptr;
     rr_server *S = new (std::nothrow) rr_server();

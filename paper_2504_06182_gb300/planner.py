@@ -7,9 +7,9 @@ import ctypes
 
 import torch
 
-from . import (RR_BIRD, RR_BITS32, RR_ERR_CAPACITY, RR_INFEASIBLE, RR_OK, RR_U8, RR_WITH_BATCH, RRError,
-               rr_batch, rr_bird_plan, rr_ctx_create, rr_ctx_destroy, rr_instance, rr_last_error, rr_plan,
-               rr_plan_batched, rr_rect)
+from . import (RR_BIRD, RR_BITS32, RR_ERR_CAPACITY, RR_INFEASIBLE, RR_OK, RR_STRICT_RESERVOIR, RR_U8,
+               RR_WITH_BATCH, RRError, rr_batch, rr_ctx_create, rr_ctx_destroy, rr_instance, rr_last_error,
+               rr_plan_batched, rr_plan_mode, rr_rect)
 
 INSTANCE_BYTES = ctypes.sizeof(rr_instance)
 
@@ -34,9 +34,10 @@ class Planner:
             raise RRError(st, rr_last_error(self.ctx))
 
     def plan(self, grid: torch.Tensor, rect, layout: int = RR_U8, n: int | None = None, cap: int | None = None,
-             bird: bool = False):
+             bird: bool = False, strict: bool = False):
         """grid: device tensor, (m, n) uint8 or (m, ceil(n/32)) int32 words.
-        bird: plan with the bird algorithm instead of red-rec.
+        bird: plan with the bird algorithm instead of red-rec; strict: the
+        strict-reservoir reading of target sub-rectangles.
         Returns (status, moves (k, 4) int32 device tensor)."""
         m = grid.shape[0]
         if n is None:
@@ -44,9 +45,10 @@ class Planner:
         if cap is None:
             cap = max(64, 2 * m * n)
         moves = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=grid.device)
-        st, k = (rr_bird_plan if bird else rr_plan)(self.ctx, grid, layout, m, n, rect, moves, cap)
+        flags = (RR_BIRD if bird else 0) | (RR_STRICT_RESERVOIR if strict else 0)
+        st, k = rr_plan_mode(self.ctx, grid, layout, m, n, rect, flags, moves, cap)
         if st == RR_ERR_CAPACITY:
-            return self.plan(grid, rect, layout, n, cap=k, bird=bird)
+            return self.plan(grid, rect, layout, n, cap=k, bird=bird, strict=strict)
         self._check(st, (RR_OK, RR_INFEASIBLE))
         return st, moves[:k]
 
@@ -93,8 +95,8 @@ def unpack_instances(dev_tensor: torch.Tensor, count: int):
 
 
 def plan_batched(planner: Planner, inst_tensor: torch.Tensor, count: int, max_side: int, with_batch=True,
-                 stream=None, bird=False):
-    flags = (RR_WITH_BATCH if with_batch else 0) | (RR_BIRD if bird else 0)
+                 stream=None, bird=False, strict=False):
+    flags = (RR_WITH_BATCH if with_batch else 0) | (RR_BIRD if bird else 0) | (RR_STRICT_RESERVOIR if strict else 0)
     st = rr_plan_batched(planner.ctx, inst_tensor, count, max_side, flags, stream)
     if st != RR_OK:
         raise RRError(st, rr_last_error(planner.ctx))

@@ -221,3 +221,51 @@ def test_bird_served():
             assert rr.rr_serve_release(srv, t) == rr.RR_OK
     finally:
         rr.rr_serve_close(srv)
+
+
+@pytest.mark.parametrize("bird", [False, True])
+def test_strict_reservoir_mode(planner, bird):
+    """RR_STRICT_RESERVOIR (outer columns donate only their reservoir-row
+    atoms) for red-rec and bird: random rectangles, both layouts, plans equal
+    the oracle's strict plans; batched calls with the flag too."""
+    import paper_2504_06182_gb300 as rr
+    from paper_2504_06182_gb300.planner import pack_instances, plan_batched, unpack_instances
+    rng = np.random.default_rng(99)
+    f = oracle.bird if bird else oracle.plan
+    feasible = 0
+    cases = [random_case(rng) for _ in range(200)]
+    for t, (grid, rect) in enumerate(cases):
+        ref = f(grid, rect, strict=True)
+        m, n = grid.shape
+        layout = rr.RR_U8 if t % 2 else rr.RR_BITS32
+        st, mv = planner.plan(to_device(grid, layout), rect, layout=layout, n=n, bird=bird, strict=True)
+        assert st == ref.status, (t, st, ref.status)
+        assert (mv.cpu().numpy() == ref.moves).all() and mv.shape[0] == len(ref.moves)
+        feasible += ref.status == 0
+    assert feasible > 50
+    # batched, with batching
+    entries, outs, refs = [], [], []
+    for grid, rect in cases[:40]:
+        ref = f(grid, rect, strict=True)
+        m, n = grid.shape
+        k = max(len(ref.moves), 1)
+        steps = int((np.abs(ref.moves[:, 0] - ref.moves[:, 2]) + np.abs(ref.moves[:, 1] - ref.moves[:, 3])).sum()) \
+            if len(ref.moves) else 0
+        mv = torch.empty((k, 4), dtype=torch.int32, device="cuda")
+        ops = torch.empty((max(steps, 1), 3), dtype=torch.int32, device="cuda")
+        mem = torch.empty((max(steps, 1),), dtype=torch.int32, device="cuda")
+        entries.append(dict(grid=to_device(grid, rr.RR_U8), layout=rr.RR_U8, m=m, n=n, rect=rect, moves=mv,
+                            cap_moves=k, ops=ops, cap_ops=max(steps, 1), members=mem, cap_members=max(steps, 1)))
+        outs.append((mv, ops, mem))
+        refs.append((grid, ref))
+    dev = pack_instances(entries)
+    plan_batched(planner, dev, len(entries), 70, with_batch=True, bird=bird, strict=True)
+    torch.cuda.synchronize()
+    for (grid, ref), r, (mv, ops, mem) in zip(refs, unpack_instances(dev, len(entries)), outs):
+        assert r.status == (rr.RR_OK if ref.status == 0 else rr.RR_INFEASIBLE)
+        assert r.n_moves == len(ref.moves)
+        if ref.status == 0:
+            assert (mv[: r.n_moves].cpu().numpy() == ref.moves).all()
+            rops, rmem = oracle.batch(ref.moves, *grid.shape)
+            assert r.n_ops == len(rops) and (ops[: r.n_ops].cpu().numpy() == rops).all()
+            assert r.n_members == len(rmem) and (mem[: r.n_members].cpu().numpy() == rmem).all()
