@@ -180,7 +180,7 @@ __device__ int bird_side(const uint32_t *bits, int W, int m, int n, int r0, int 
 __global__ void __launch_bounds__(64) k_bird(rr_instance *inst, JobWS *wsv, int count, int max_side)
 {
     extern __shared__ uint32_t birdsm[];
-    __shared__ int s_nt, s_nb, s_a, s_base, s_bad, s_cnt[2];
+    __shared__ int s_nt, s_nb, s_a, s_base, s_bad, s_nrecv, s_cnt[2];
     const int q = blockIdx.x;
     if (q >= count) return;
     rr_instance *I = &inst[q];
@@ -194,6 +194,11 @@ __global__ void __launch_bounds__(64) k_bird(rr_instance *inst, JobWS *wsv, int 
     while (listCap < max_side) listCap <<= 1;
     int32_t *topTok = (int32_t *)(birdsm + (size_t)max_side * ((max_side + 31) >> 5));
     int32_t *botTok = topTok + listCap;
+    // receivers in column order (column, band atoms, atoms above the band),
+    // and the current receiver's band holes and band atom rows
+    int16_t *recvCol = (int16_t *)(botTok + listCap);
+    int16_t *recvM = recvCol + max_side, *recvTop = recvM + max_side;
+    int16_t *sHr = recvTop + max_side, *sOwn = sHr + max_side;
 
     // Feasibility (total surplus, Sec. III.C) and the offsets of the column
     // units, in column order.
@@ -213,6 +218,21 @@ __global__ void __launch_bounds__(64) k_bird(rr_instance *inst, JobWS *wsv, int 
             s_base = carry;
             s_bad = tot < 0;
         }
+    } else if (wid == 1) {
+        int nr = 0;
+        for (int base = c0; base < c1; base += 32) {
+            const int c = base + lane;
+            bool rc = false;
+            int M = 0, T = 0;
+            if (c < c1) { const ColInfo ci = ws.col[c]; rc = ci.kind == KIND_RECEIVER; M = ci.nband; T = ci.ntop; }
+            const unsigned bal = __ballot_sync(FULL, rc);
+            if (rc) {
+                const int at = nr + __popc(bal & ((1u << lane) - 1u));
+                recvCol[at] = (int16_t)c; recvM[at] = (int16_t)M; recvTop[at] = (int16_t)T;
+            }
+            nr += __popc(bal);
+        }
+        if (lane == 0) s_nrecv = nr;
     }
     // Reservoir rows after the column phase: solved target columns keep the
     // atoms outside their window, outer columns with enough atoms fill every
@@ -239,13 +259,21 @@ __global__ void __launch_bounds__(64) k_bird(rr_instance *inst, JobWS *wsv, int 
     }
 
     const long long colTotal = s_base;
+    const int nrecv = s_nrecv;
     long long done = 0;          // moves of the receiver units so far
     long long steps = 0;
-    for (int j = c0; j < c1; ++j) {
-        const ColInfo Rj = ws.col[j];
-        if (Rj.kind != KIND_RECEIVER) continue;
-        const int M = Rj.nband, need = h - M, nh = h - M;
-        const int16_t *hr = ws.holeRows + (size_t)(j - c0) * h;
+    for (int u = 0; u < nrecv; ++u) {
+        const int j = recvCol[u], M = recvM[u], ownTop = recvTop[u];
+        const int need = h - M, nh = h - M;
+        // this receiver's band holes and band atoms (read by the split and
+        // the emission once the walks are done)
+        {
+            const int16_t *ghr = ws.holeRows + (size_t)(j - c0) * h;
+            const int16_t *gown = ws.atomRows + (size_t)j * m + ownTop;
+            for (int t = tid; t < nh; t += blockDim.x) sHr[t] = ghr[t];
+            for (int t = tid; t < M; t += blockDim.x) sOwn[t] = gown[t];
+        }
+        const int16_t *hr = sHr;
         if (wid < 2) {
             const int got = bird_side(bits, W, m, n, r0, r1, j, wid == 0, need, wid == 0 ? topTok : botTok,
                                       &s_cnt[wid]);
@@ -281,12 +309,11 @@ __global__ void __launch_bounds__(64) k_bird(rr_instance *inst, JobWS *wsv, int 
         // rows shallowest first; isolated band atoms are dropped.
         const int kd_end = a + band_P(hr, nh, M, r0, r0 + a - 1);
         const int ku_start = a + band_P(hr, nh, M, r0, r0 + a);
-        const int16_t *own = ws.atomRows + (size_t)j * m;
         const long long base = colTotal + done;
         for (int k = tid; k < h; k += blockDim.x) {
             int row, col;
             if (k < a) { const int v = topTok[a - 1 - k]; row = tok_row(v); col = tok_col(v); }
-            else if (k < a + M) { row = own[Rj.ntop + (k - a)]; col = j; }
+            else if (k < a + M) { row = sOwn[k - a]; col = j; }
             else { const int v = botTok[k - a - M]; row = tok_row(v); col = tok_col(v); }
             int pos;
             if (k < kd_end) pos = kd_end - 1 - k;

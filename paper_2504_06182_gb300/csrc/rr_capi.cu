@@ -296,13 +296,15 @@ static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v
 static int budget(const rr_ctx *ctx, int base) { return ctx->shift >= 0 ? base << ctx->shift : base >> -ctx->shift; }
 
 // Shared memory of a k_bird block: reservoir-row bits of the largest grid
-// (column-major, one word per 32 rows) and the two token lists (each the
-// next power of two >= max_side: they double as sort buffers).
+// (column-major, one word per 32 rows), the two token lists (each the next
+// power of two >= max_side: they double as sort buffers), then five int16
+// arrays of max_side (the receiver list: columns, band atoms, atoms above
+// the band; the current receiver's band holes and band atom rows).
 static size_t bird_smem_bytes(int max_side)
 {
     size_t cap = 1;
     while (cap < (size_t)max_side) cap <<= 1;
-    return 4 * ((size_t)max_side * ((max_side + 31) / 32) + 2 * cap);
+    return 4 * ((size_t)max_side * ((max_side + 31) / 32) + 2 * cap) + 2 * 5 * (size_t)max_side;
 }
 
 // Planning kernels over `count` device descriptors whose sides are <= max_side:
