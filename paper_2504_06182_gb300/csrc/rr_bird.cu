@@ -113,37 +113,79 @@ __device__ void warp_sort_u32(uint32_t *a, int len)
         }
 }
 
+// Smallest layer K >= lo at which one side holds `need` tokens, kmax when it
+// never does (one warp); the layers below lo hold fewer. The search starts
+// from `guess` (the previous receiver's cut-off on this side: the
+// reservoirs change little from one column to the next), gallops toward the
+// answer, then bisects. *before gets the tokens in layers < K.
+__device__ int find_cutoff(const uint32_t *bits, int W, int m, int n, int r0, int r1, int j, bool top, int need,
+                           int lo, int kmax, int guess, int *before)
+{
+    int kb = lo - 1, cb = kb < 0 ? 0 : -1;   // largest layer known to hold fewer than need, its count
+    const int g = min(max(guess, lo), kmax);
+    int hi = kmax;
+    const int cg = side_count(bits, W, m, n, r0, r1, j, top, g);
+    if (cg >= need) {
+        hi = g;
+        for (int s = 1; hi - s >= lo; s <<= 1) {
+            const int t = hi - s;
+            const int ct = side_count(bits, W, m, n, r0, r1, j, top, t);
+            if (ct >= need) { hi = t; continue; }
+            kb = t; cb = ct; lo = t + 1;
+            break;
+        }
+    } else {
+        kb = g; cb = cg; lo = g + 1;
+        for (int s = 1;; s <<= 1) {
+            const int t = min(g + s, kmax);
+            const int ct = side_count(bits, W, m, n, r0, r1, j, top, t);
+            if (ct >= need) { hi = t; break; }
+            kb = t; cb = ct; lo = t + 1;
+            if (t == kmax) {                    // fewer than need in all: take them all
+                *before = side_count(bits, W, m, n, r0, r1, j, top, kmax - 1);
+                return kmax;
+            }
+        }
+    }
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const int cm = side_count(bits, W, m, n, r0, r1, j, top, mid);
+        if (cm >= need) hi = mid;
+        else { lo = mid + 1; kb = mid; cb = cm; }
+    }
+    *before = lo == 0 ? 0 : (kb == lo - 1 && cb >= 0 ? cb : side_count(bits, W, m, n, r0, r1, j, top, lo - 1));
+    return lo;
+}
+
 // Collects, in walk order, the `need` nearest tokens of receiver j on one
 // side of the band, or all of them if fewer (one warp). While the
 // reservoirs near j are full the walk finds them in a few iterations. Once
-// they are depleted the walk would scan the empty area cell by cell, so
-// after a bounded walk the cut-off layer K (the first at which the count
-// reaches need) is found by binary search over per-column popcounts; the
-// tokens of the layers before K are gathered by their walk index and
-// sorted, and layer K alone is walked.
+// they are depleted the walk would scan the empty area cell by cell, so the
+// cut-off layer K (the first at which the count reaches need) is found by
+// popcounts instead (find_cutoff); the tokens of the layers before K are
+// gathered by their walk index and sorted, and layer K alone is walked.
+// *sparse and *kHint carry this side's state from one receiver to the next:
+// after a cut-off beyond what the bounded walk would have reached, the next
+// receiver skips the walk and starts the search from this cut-off.
 __device__ int bird_side(const uint32_t *bits, int W, int m, int n, int r0, int r1, int j, bool top, int need,
-                         int32_t *list, int *s_cnt)
+                         int32_t *list, int *s_cnt, bool *sparse, int *kHint)
 {
     const int lane = threadIdx.x & 31;
     if (top ? r0 == 0 : r1 == m) return 0;
     const int dmax = max(j, n - 1 - j);
     const int kmax = top ? r0 - 1 + dmax : m - 1 - r1 + dmax;   // no cell beyond this layer
     const int gAll = (kmax + 1) * (kmax + 1);
-    int gNext;
-    int got = walk_range(bits, W, m, n, r0, r1, j, top, need, 0, gAll, 8 + need / 8, 0, list, &gNext);
-    if (got >= need || gNext >= gAll) return got;
-    // layers below the walk's last one hold fewer than need tokens
-    int lo = isqrt_floor(gNext), hi = kmax;
-    if (side_count(bits, W, m, n, r0, r1, j, top, kmax) >= need) {
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (side_count(bits, W, m, n, r0, r1, j, top, mid) >= need) hi = mid; else lo = mid + 1;
-        }
-    } else {
-        lo = kmax;
+    const int walkIter = 8 + need / 8;
+    int gNext, lo = 0;
+    if (!*sparse) {
+        const int got = walk_range(bits, W, m, n, r0, r1, j, top, need, 0, gAll, walkIter, 0, list, &gNext);
+        if (got >= need || gNext >= gAll) return got;
+        lo = isqrt_floor(gNext);             // layers below the walk's last one hold fewer than need
     }
-    const int K = lo;
-    const int before = K > 0 ? side_count(bits, W, m, n, r0, r1, j, top, K - 1) : 0;
+    int before;
+    const int K = find_cutoff(bits, W, m, n, r0, r1, j, top, need, lo, kmax, *kHint, &before);
+    *kHint = K;
+    *sparse = (K + 1) * (K + 1) > 32 * walkIter;
     // gather the walk indices of the tokens in layers < K, sort, decode
     if (lane == 0) *s_cnt = 0;
     __syncwarp();
@@ -262,6 +304,8 @@ __global__ void __launch_bounds__(64) k_bird(rr_instance *inst, JobWS *wsv, int 
     const int nrecv = s_nrecv;
     long long done = 0;          // moves of the receiver units so far
     long long steps = 0;
+    bool sparse = false;         // this warp's side: walk skipped, search hint
+    int kHint = 0;
     for (int u = 0; u < nrecv; ++u) {
         const int j = recvCol[u], M = recvM[u], ownTop = recvTop[u];
         const int need = h - M, nh = h - M;
@@ -276,7 +320,7 @@ __global__ void __launch_bounds__(64) k_bird(rr_instance *inst, JobWS *wsv, int 
         const int16_t *hr = sHr;
         if (wid < 2) {
             const int got = bird_side(bits, W, m, n, r0, r1, j, wid == 0, need, wid == 0 ? topTok : botTok,
-                                      &s_cnt[wid]);
+                                      &s_cnt[wid], &sparse, &kHint);
             if (lane == 0) { if (wid == 0) s_nt = got; else s_nb = got; }
         }
         __syncthreads();
