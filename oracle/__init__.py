@@ -33,25 +33,33 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+def load(path: str):
+    """Loads an oracle library from `path` and declares its entry points."""
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int, ctypes.c_int64
+    L.rro_window.argtypes = [P, i32, i32, i32]
+    L.rro_window.restype = i32
+    L.rro_split.argtypes = [P, i32, P, i32, P, i32, i32, i32, i32, P]
+    L.rro_split.restype = i32
+    L.rro_plan_mode.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, i64, P, i32]
+    L.rro_plan_mode.restype = i32
+    L.rro_bird_mode.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, i64, P, i32]
+    L.rro_bird_mode.restype = i32
+    L.rro_batch.argtypes = [P, i64, i32, i32, P, i64, P, i64, P, P]
+    L.rro_batch.restype = i32
+    L.rro_batch_prefix.argtypes = [P, i64, i32, i32, i64, P, i64, P, i64, P, P]
+    L.rro_batch_prefix.restype = i32
+    return L
+
+
 def lib():
+    """The oracle library: the one built here, or the one named by
+    RR_ORACLE_LIB (the pin-strength test points it at deliberately broken
+    copies of the oracle)."""
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
-        P = ctypes.c_void_p
-        i32, i64 = ctypes.c_int, ctypes.c_int64
-        L.rro_window.argtypes = [P, i32, i32, i32]
-        L.rro_window.restype = i32
-        L.rro_split.argtypes = [P, i32, P, i32, P, i32, i32, i32, i32, P]
-        L.rro_split.restype = i32
-        L.rro_plan_mode.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, i64, P, i32]
-        L.rro_plan_mode.restype = i32
-        L.rro_bird_mode.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, i64, P, i32]
-        L.rro_bird_mode.restype = i32
-        L.rro_batch.argtypes = [P, i64, i32, i32, P, i64, P, i64, P, P]
-        L.rro_batch.restype = i32
-        L.rro_batch_prefix.argtypes = [P, i64, i32, i32, i64, P, i64, P, i64, P, P]
-        L.rro_batch_prefix.restype = i32
-        _lib = L
+        _lib = load(os.environ.get("RR_ORACLE_LIB") or build())
     return _lib
 
 

@@ -143,6 +143,22 @@ def test_window_exhaustive_subsets():
             assert cost == best
 
 
+def test_split_ties_take_the_largest_a():
+    """Reading 6 (Sec. III.C leaves ties open): among choices of equal total
+    distance the split takes the most atoms from above the band. One target
+    row r0 = 4 (h = 1), one pool atom one row above (3) and one one row below
+    (5): both cost 1, so a = 1 (the atom above)."""
+    a, cost = oracle.split([], [3], [5], 1, 4, 1)
+    assert (a, cost) == (1, 1)
+    # two targets, rows 4 and 5; pool rows 2, 3 above and 6, 7 below: the
+    # split against the cost of every a, written out here
+    a, cost = oracle.split([], [2, 3], [6, 7], 2, 4, 2)
+    costs = {aa: sum(abs(r - t) for r, t in zip(sorted([2, 3][2 - aa:] + [6, 7][:2 - aa]), [4, 5]))
+             for aa in range(3)}
+    best = min(costs.values())
+    assert cost == best and a == max(aa for aa, c in costs.items() if c == best)
+
+
 def test_split_optimal_over_all_subsets():
     """P2 for the redistribution instance (Sec. III.C): choosing the a nearest
     pool atoms above and x-a nearest below is as good as the best of all
