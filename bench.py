@@ -7,6 +7,13 @@ floor(0.7 * side), bit-packed uint32 rows; the whole batch is planned
 (Alg. 1) and batched (Alg. 4) by one rr_plan_batched(RR_WITH_BATCH) call.
 Inputs are seeded synthetic grids (gridgen), resident in HBM before timing.
 
+The line also carries, measured after the timed steps: the same grids
+replayed from a captured CUDA graph and end to end with host copies; the
+plain one-grid-per-call path; the paper's runtime geometry (red-rec and bird
+plans against the single-thread oracle); the served stream; and the bird
+planner (Alg. 2) with batching on the same grids (`bird`, with its own CPU
+oracle sample).
+
 `--impl reference` times the CPU oracle instead (bounded samples of the same
 workload on the host cores). Under torchrun every rank plans its own 4096
 grids (weak scaling); rank 0 prints one JSON line.
