@@ -46,6 +46,8 @@ def load(path: str):
     L.rro_plan_mode.restype = i32
     L.rro_bird_mode.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, P, i64, P, i32]
     L.rro_bird_mode.restype = i32
+    L.rro_bird_prefix.argtypes = [P, i32, i32, i32, i32, i32, i32, P, i64, P, i64]
+    L.rro_bird_prefix.restype = i32
     L.rro_batch.argtypes = [P, i64, i32, i32, P, i64, P, i64, P, P]
     L.rro_batch.restype = i32
     L.rro_batch_prefix.argtypes = [P, i64, i32, i32, i64, P, i64, P, i64, P, P]
@@ -141,6 +143,26 @@ def bird(grid: np.ndarray, rect, with_trace: bool = False, strict: bool = False)
     if st not in (OK, INFEASIBLE):
         raise RuntimeError(f"oracle rro_bird failed with status {st}")
     return Plan(st, moves[: nm.value].copy(), None, units[: nu.value].copy() if with_trace else None)
+
+
+def bird_prefix(grid: np.ndarray, rect, max_units: int) -> Plan:
+    """The bird planner stopped after its first max_units receiver units."""
+    grid = np.ascontiguousarray(grid, dtype=np.uint8)
+    m, n = grid.shape
+    r0, c0, r1, c1 = (int(v) for v in rect)
+    nm = ctypes.c_int64(0)
+    cap = 0
+    while True:
+        moves = np.zeros((max(cap, 1), 4), dtype=np.int32)
+        st = lib().rro_bird_prefix(_ptr(grid), m, n, r0, c0, r1, c1, _ptr(moves), cap, ctypes.byref(nm),
+                                   int(max_units))
+        if st == ERR_CAPACITY:
+            cap = nm.value
+            continue
+        break
+    if st not in (OK, INFEASIBLE):
+        raise RuntimeError(f"oracle rro_bird_prefix failed with status {st}")
+    return Plan(st, moves[: nm.value].copy(), None, None)
 
 
 def batch(moves: np.ndarray, m: int, n: int, max_ops: int | None = None, cap: int = 0):

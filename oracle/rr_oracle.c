@@ -471,16 +471,36 @@ static void apply_unit(uint8_t *cur, int n, const mv_t *u, int cnt)
     for (int k = 0; k < cnt; ++k) cur[(size_t)u[k].dr * n + u[k].dc] = 1;
 }
 
+static int bird_impl(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
+                     int32_t *moves, int64_t cap, int64_t *n_moves,
+                     int32_t *units, int64_t cap_units, int64_t *n_units, int strict,
+                     int64_t max_units);
+
 int rro_bird(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
              int32_t *moves, int64_t cap, int64_t *n_moves,
              int32_t *units, int64_t cap_units, int64_t *n_units)
 {
-    return rro_bird_mode(grid, m, n, r0, c0, r1, c1, moves, cap, n_moves, units, cap_units, n_units, 0);
+    return bird_impl(grid, m, n, r0, c0, r1, c1, moves, cap, n_moves, units, cap_units, n_units, 0, -1);
 }
 
 int rro_bird_mode(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
                   int32_t *moves, int64_t cap, int64_t *n_moves,
                   int32_t *units, int64_t cap_units, int64_t *n_units, int strict)
+{
+    return bird_impl(grid, m, n, r0, c0, r1, c1, moves, cap, n_moves, units, cap_units, n_units, strict, -1);
+}
+
+int rro_bird_prefix(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
+                    int32_t *moves, int64_t cap, int64_t *n_moves, int64_t max_units)
+{
+    if (max_units < 0) return E_ARG;
+    return bird_impl(grid, m, n, r0, c0, r1, c1, moves, cap, n_moves, NULL, 0, NULL, 0, max_units);
+}
+
+static int bird_impl(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
+                     int32_t *moves, int64_t cap, int64_t *n_moves,
+                     int32_t *units, int64_t cap_units, int64_t *n_units, int strict,
+                     int64_t max_units)
 {
     if (!grid || !n_moves || m < 1 || n < 1 || r0 < 0 || r0 >= r1 || r1 > m ||
         c0 < 0 || c0 >= c1 || c1 > n || cap < 0 || (cap > 0 && !moves))
@@ -530,6 +550,7 @@ int rro_bird_mode(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int
      * instance; then the next one. */
     for (int j = c0; j < c1; ++j) {
         if (!recv[j]) continue;
+        if (max_units >= 0 && nu >= max_units) break;
         int nt = 0;
         for (int c = 0; c < n; ++c)
             for (int r = 0; r < m; ++r) {

@@ -81,6 +81,12 @@ int rro_bird_mode(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int
                   int32_t *moves, int64_t cap, int64_t *n_moves,
                   int32_t *units, int64_t cap_units, int64_t *n_units, int strict);
 
+/* The same planner stopped after its first max_units receiver units (the
+ * column phase and a leading sample of the move list, for grids too large
+ * to plan completely this way). */
+int rro_bird_prefix(const uint8_t *grid, int m, int n, int r0, int c0, int r1, int c1,
+                    int32_t *moves, int64_t cap, int64_t *n_moves, int64_t max_units);
+
 /* The batching routine (Alg. 4 with the local constraint set of Sec. IV).
  * ops: cap_ops*3 int32; members: cap_members int32. */
 int rro_batch(const int32_t *moves, int64_t n_moves, int m, int n,

@@ -168,9 +168,10 @@ def test_bird_capacity_and_infeasible(planner):
 
 def test_bird_grid_1024_replay(planner):
     """Full-size 1024 x 1024 grid with a centred 720 x 720 target (too large
-    for the oracle's literal window scan): the GPU's bird plan starts with
-    red-rec's column phase (itself equal to the oracle's), replays without
-    obstruction and fills the target."""
+    for the oracle's literal window scan over the whole plan): the GPU's bird
+    plan equals the oracle's for the column phase and the first eight
+    receiver units (the oracle stopped there), starts with red-rec's column
+    phase, replays without obstruction and fills the target."""
     from paper_2504_06182_gb300 import RR_BITS32
     inst = gridgen.square_instance(0, 0, 1024, 0.6, 720)
     g = to_device(inst.grid, RR_BITS32)
@@ -186,6 +187,9 @@ def test_bird_grid_1024_replay(planner):
     ncol = int(np.argmax(recv[mv[:, 3]]))
     assert ncol > 0 and ncol == int(np.argmax(recv[rmv[:, 3]]))
     assert (mv[:ncol] == rmv[:ncol]).all()
+    pref = oracle.bird_prefix(inst.grid, inst.rect, 8)
+    assert len(pref.moves) > ncol
+    assert (mv[: len(pref.moves)] == pref.moves).all()
     final = replay_moves(inst.grid, inst.rect, mv)
     assert_target_full(final, inst.rect, inst.grid)
 

@@ -184,3 +184,17 @@ def test_bird_prefers_nearby_tokens_over_one_donor():
         checked += 1
         assert path_len(b.moves) <= path_len(r.moves)
     assert checked > 50
+
+
+def test_bird_prefix_is_a_prefix():
+    """rro_bird_prefix (used for full-size sampled parity) stops after its
+    first receiver units: its moves are the leading moves of the full plan."""
+    for seed in range(12):
+        inst = square_instance(seed, 21, 24 + seed, 0.55)
+        full = oracle.bird(inst.grid, inst.rect, with_trace=True)
+        if full.status != 0:
+            continue
+        for u in (0, 1, 2, len(full.events)):
+            p = oracle.bird_prefix(inst.grid, inst.rect, u)
+            assert p.moves.tolist() == full.moves[: len(p.moves)].tolist()
+        assert len(oracle.bird_prefix(inst.grid, inst.rect, len(full.events)).moves) == len(full.moves)
