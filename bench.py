@@ -793,13 +793,17 @@ def run_configs(args):
     seeds = list(range(10))
     cpu = {}
     for name, side, t, _ in SINGLE_CONFIGS:
-        plan_us, both_us, sample = [], [], ""
+        plan_us, both_us, bird_us, sample = [], [], [], ""
         for sd in (seeds if side < 1024 else seeds[:3]):
             inst = gridgen.square_instance(sd, 0, side, 0.6, t)
             t0 = time.perf_counter()
             p = oracle.plan(inst.grid, inst.rect)
             t1 = time.perf_counter()
             plan_us.append((t1 - t0) * 1e6)
+            if side < 1024:      # the oracle's bird scans every window: too slow beyond 256^2
+                tb = time.perf_counter()
+                oracle.bird(inst.grid, inst.rect)
+                bird_us.append((time.perf_counter() - tb) * 1e6)
             if side < 1024:
                 oracle.batch(p.moves, side, side, cap=path_steps(p.moves))
                 both_us.append((time.perf_counter() - t0) * 1e6)
@@ -811,6 +815,7 @@ def run_configs(args):
                          f"at {rate:.0f} batches/s"
         cpu[side] = {"kind": "oracle", "cores": 1, "plan_us": float(np.median(plan_us)),
                      "plan_batch_us": float(np.median(both_us)) if both_us else None,
+                     "bird_plan_us": float(np.median(bird_us)) if bird_us else None,
                      "sample": sample or f"seeds 0..{seeds[-1]}, one grid at a time"}
     cpu_chain = oracle_chain_us()
     import torch
@@ -819,7 +824,7 @@ def run_configs(args):
     P = Planner(arena_bytes=4 << 30)
     for name, side, t, lay in SINGLE_CONFIGS:
         layout = rr.RR_U8 if lay == "u8" else rr.RR_BITS32
-        plan_us, both_us, outs = [], [], None
+        plan_us, both_us, bird_us, outs = [], [], [], None
         for sd in seeds:
             inst = gridgen.square_instance(sd, 0, side, 0.6, t)
             host = inst.grid if lay == "u8" else gridgen.pack_bits32(inst.grid).view(np.int32)
@@ -836,16 +841,23 @@ def run_configs(args):
                 res = P.batch(mv, side, side) if st == rr.RR_OK and len(mv) else None
                 torch.cuda.synchronize()
                 return st, mv, res
+            def bird():
+                r = P.plan(g, inst.rect, layout=layout, n=side, cap=cap, bird=True)
+                torch.cuda.synchronize()
+                return r
             both()
+            bird()
             reps = 20 if side <= 256 else 2
             plan_us.append(median_us(plan, reps))
             both_us.append(median_us(both, max(2, reps // 4)))
+            bird_us.append(median_us(bird, reps))
             if sd == 0:
                 st, mv, res = both()
                 outs = {"status": int(st), "moves": int(len(mv)),
                         "ops": int(len(res[0])) if res else 0, "steps": int(len(res[1])) if res else 0}
         line = {"config": name, "metric": "plain per-grid latency (median over seeds 0..9)", "unit": "us",
                 "gpu": {"plan_us": float(np.median(plan_us)), "plan_batch_us": float(np.median(both_us)),
+                        "bird_plan_us": float(np.median(bird_us)),
                         "path": "one rr_plan (and rr_batch) call per grid, grid resident on the device, synchronised"},
                 "cpu_baseline": cpu[side], "seed0_outputs": outs, "data": "synthetic"}
         print(json.dumps(line), flush=True)
