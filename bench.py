@@ -800,13 +800,13 @@ def run_configs(args):
             p = oracle.plan(inst.grid, inst.rect)
             t1 = time.perf_counter()
             plan_us.append((t1 - t0) * 1e6)
-            if side < 1024:      # the oracle's bird scans every window: too slow beyond 256^2
-                tb = time.perf_counter()
-                oracle.bird(inst.grid, inst.rect)
-                bird_us.append((time.perf_counter() - tb) * 1e6)
             if side < 1024:
                 oracle.batch(p.moves, side, side, cap=path_steps(p.moves))
                 both_us.append((time.perf_counter() - t0) * 1e6)
+                # the oracle's bird scans every window: too slow beyond 256^2
+                tb = time.perf_counter()
+                oracle.bird(inst.grid, inst.rect)
+                bird_us.append((time.perf_counter() - tb) * 1e6)
             elif sd == 0:
                 t2 = time.perf_counter()
                 ops, _ = oracle.batch(p.moves, side, side, max_ops=200000, cap=path_steps(p.moves))
