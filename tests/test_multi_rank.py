@@ -4,7 +4,6 @@ collectives are the barrier and the maximum of the ranks' times."""
 import os
 import socket
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
