@@ -191,9 +191,8 @@ extern "C" int rr_ctx_create(rr_ctx **out, int64_t arena_bytes)
     rr_ctx *ctx = nullptr;
     if (!out) return fail(nullptr, RR_ERR_ARG, "rr_ctx_create: null output pointer");
     *out = nullptr;
-    ctx = new (std::nothrow) rr_ctx();
+    ctx = new (std::nothrow) rr_ctx();   // value-initialised: every member zero, then its initialiser
     if (!ctx) return fail(nullptr, RR_ERR_ARG, "rr_ctx_create: out of host memory");
-    std::memset(ctx, 0, sizeof(*ctx));
     ctx->nclass = 4;
     ctx->shift = 0;
     ctx->pipe = 1;
