@@ -38,4 +38,4 @@ def test_golden(path):
 
 
 def test_golden_fixture_count():
-    assert len(GOLDEN) >= 8
+    assert len(GOLDEN) >= 10

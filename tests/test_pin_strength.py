@@ -39,6 +39,11 @@ MUTANTS = [
     ("batch_without_same_line", "ok = accr[a] == r || accc[a] == c;", "ok = 1;", 0),
     ("batch_without_same_direction", "ok = d == d0;", "ok = 1;", 0),
     ("gamma_ignores_shared_vertices", "if (cover[off[v]] != b) blocked[b]++;", "if (0) blocked[b]++;", 0),
+    ("bird_receivers_right_to_left", "for (int j = c0; j < c1; ++j) {", "for (int j = c1 - 1; j >= c0; --j) {", 0),
+    ("strict_mode_ignored_in_redrec", "} else if (!strict && K[c] >= R) {", "} else if (K[c] >= R) {", 0),
+    ("strict_mode_ignored_in_bird", "} else if (!strict && K >= R) {", "} else if (K >= R) {", 0),
+    ("bird_skips_unsolved_columns", "if (c == j) T[nt++] = (btok_t){r, r, c};",
+     "if (c == j) T[nt++] = (btok_t){r, r, c};\n                else if (recv[c]) continue;", 0),
 ]
 
 
