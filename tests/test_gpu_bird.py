@@ -273,3 +273,32 @@ def test_strict_reservoir_mode(planner, bird):
             rops, rmem = oracle.batch(ref.moves, *grid.shape)
             assert r.n_ops == len(rops) and (ops[: r.n_ops].cpu().numpy() == rops).all()
             assert r.n_members == len(rmem) and (mem[: r.n_members].cpu().numpy() == rmem).all()
+
+
+def test_bird_edge_cases(planner):
+    """Adversarial shapes for bird (and its strict mode): no atoms, a full
+    grid, a target covering the grid, h = m, 1 x 1, one column, one row, every
+    column at zero surplus, ragged 32-tiles."""
+    import paper_2504_06182_gb300 as rr
+    rng = np.random.default_rng(8)
+    cases = [(np.zeros((8, 8), np.uint8), (2, 2, 6, 6)),
+             (np.ones((8, 8), np.uint8), (2, 2, 6, 6)),
+             (np.ones((5, 7), np.uint8), (0, 0, 5, 7)),
+             (np.ones((1, 1), np.uint8), (0, 0, 1, 1)),
+             ((rng.random((97, 1)) < 0.6).astype(np.uint8), (30, 0, 60, 1)),
+             ((rng.random((1, 97)) < 0.9).astype(np.uint8), (0, 3, 1, 90)),
+             ((rng.random((65, 65)) < 0.6).astype(np.uint8), (10, 10, 55, 55))]
+    g = np.ones((6, 4), np.uint8); g[3, 1] = 0
+    cases.append((g, (0, 1, 6, 3)))                                   # h = m, one hole
+    z = np.zeros((12, 9), np.uint8)
+    for c in range(9):                                                # 4 atoms per column, rows vary
+        z[rng.choice(12, 4, replace=False), c] = 1
+    cases.append((z, (4, 0, 8, 9)))                                   # every column at zero surplus
+    for i, (grid, rect) in enumerate(cases):
+        m, n = grid.shape
+        layout = rr.RR_U8 if i % 2 else rr.RR_BITS32
+        for strict in (False, True):
+            ref = oracle.bird(grid, rect, strict=strict)
+            st, mv = planner.plan(to_device(grid, layout), rect, layout=layout, n=n, bird=True, strict=strict)
+            assert st == ref.status, (i, strict, st, ref.status)
+            assert mv.cpu().numpy().tolist() == ref.moves.tolist(), (i, strict)
