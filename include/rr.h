@@ -248,10 +248,9 @@ int rr_serve_close(rr_server *srv);
 /* rr_plan without allocation, for callers that must not allocate device
  * memory: a real-time reconfiguration loop (cudaMalloc/cudaFree can
  * synchronise the device and take unbounded time between imaging and the
- * tweezer moves), code issuing work while a CUDA graph is being captured, or
- * a plug-in whose device memory belongs to another allocator. The paper has
- * no counterpart; the arguments, outputs and return codes are those of
- * rr_plan, and no context is used.
+ * tweezer moves), or a plug-in whose device memory belongs to another
+ * allocator. The paper has no counterpart; the arguments, outputs and return
+ * codes are those of rr_plan, and no context is used.
  * Workspace: a file-scope device array of RR_NOALLOC_SCRATCH_BYTES that every
  * GPU loading the library holds until exit. Grids above RR_NOALLOC_MAX_SIDE
  * in either side are rejected with RR_ERR_ARG. The first call on a device
@@ -259,7 +258,9 @@ int rr_serve_close(rr_server *srv);
  * call before any stream capture. All calls share the array and it keeps
  * the last call's contents: calls that overlap on the GPU (other streams,
  * other host threads) race and must be serialised by the caller.
- * Synchronises `stream`. */
+ * The call copies the move count back into host memory and synchronises
+ * `stream` before returning; on a stream that is being captured it returns
+ * RR_ERR_ARG without enqueuing anything. */
 #define RR_NOALLOC_MAX_SIDE 256
 #define RR_NOALLOC_SCRATCH_BYTES (512 * 1024)
 int rr_plan_noalloc(const void *d_grid, int layout, int m, int n, rr_rect rect,

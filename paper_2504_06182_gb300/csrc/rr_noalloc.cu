@@ -4,11 +4,14 @@
 // Who needs it: a reconfiguration control loop runs between imaging the trap
 // array and driving the tweezers, once per cycle, under a hard deadline;
 // cudaMalloc/cudaFree may synchronise the device and take unbounded time, so
-// such a loop (and code running while a CUDA graph is being captured, or a
-// plug-in whose device memory is owned by another allocator) cannot call
-// them. This entry point needs no context and allocates nothing: its
-// workspace is the file-scope array below, which every GPU that loads the
-// library holds until the process exits.
+// such a loop (and a plug-in whose device memory is owned by another
+// allocator) cannot call them. This entry point needs no context and
+// allocates nothing: its workspace is the file-scope array below, which
+// every GPU that loads the library holds until the process exits.
+//
+// The call reads the move count back into a host variable and synchronises
+// the stream before it returns, so it is refused (RR_ERR_ARG, nothing
+// enqueued) on a stream that is being captured.
 #include <cstring>
 #include "rr_internal.cuh"
 
@@ -24,12 +27,28 @@ __global__ void k_emit_recv(rr_instance *, JobWS *, int);
 using namespace rrk;
 
 // Layout: descriptor at 0, workspace table at 256, arena bump pointer at
-// 1024, arena from 4096 to the end. A 256 x 256 plan needs about 300 KB.
+// 1024, arena from 4096 to the end.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RR_NOALLOC_SCRATCH_BYTES];
 
 static constexpr size_t OFF_INST = 0, OFF_WS = 256, OFF_TOP = 1024, OFF_ARENA = 4096;
 static_assert(sizeof(rr_instance) <= OFF_WS - OFF_INST, "descriptor slot");
 static_assert(sizeof(JobWS) <= OFF_TOP - OFF_WS, "workspace table slot");
+
+// The planning set-up's arena requests for the largest accepted grid (side
+// RR_NOALLOC_MAX_SIDE, target = the whole grid), each rounded up to the
+// arena's 256-byte granule as the device allocator does.
+static constexpr size_t pad256(size_t b) { return (b + 255) & ~(size_t)255; }
+static constexpr size_t noalloc_worst_case()
+{
+    constexpr size_t S = RR_NOALLOC_MAX_SIDE, W = (S + 31) / 32;
+    return pad256(sizeof(uint32_t) * S * W) +        // bit columns
+           pad256(sizeof(int16_t) * S * S) +         // atom rows
+           pad256(sizeof(int16_t) * S * S) +         // band holes (h = m, full width)
+           pad256(sizeof(ColInfo) * S) + pad256(sizeof(RecvInfo) * S) +
+           pad256(sizeof(Event) * (S + 1)) + pad256(sizeof(int32_t) * (2 * S + 1));
+}
+static_assert(noalloc_worst_case() <= RR_NOALLOC_SCRATCH_BYTES - OFF_ARENA,
+              "the fixed workspace must hold the largest accepted plan");
 
 // Device address of the scratch array, looked up once per device (host
 // code must not use the symbol itself: it names a host-side stand-in).
@@ -56,6 +75,9 @@ extern "C" int rr_plan_noalloc(const void *d_grid, int layout, int m, int n, rr_
         m > RR_NOALLOC_MAX_SIDE || n > RR_NOALLOC_MAX_SIDE || rect.r0 < 0 || rect.r0 >= rect.r1 || rect.r1 > m ||
         rect.c0 < 0 || rect.c0 >= rect.c1 || rect.c1 > n || cap < 0 || (cap > 0 && !d_moves))
         return RR_ERR_ARG;
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap_st) != cudaSuccess) return RR_ERR_CUDA;
+    if (cap_st != cudaStreamCaptureStatusNone) return RR_ERR_ARG;   // it synchronises: not capturable
     unsigned char *base = nullptr;
     int st = scratch_for_current_device(&base);
     if (st != RR_OK) return st;

@@ -194,6 +194,30 @@ def test_bird_grid_1024_replay(planner):
     assert_target_full(final, inst.rect, inst.grid)
 
 
+def test_bird_grid_1024_full_digest(planner):
+    """The same 1024 x 1024 grid: the GPU's complete bird plan and all of its
+    batches (85.7 M of them) against the SHA-256 digests of the oracle's
+    complete outputs (tests/golden/digests_1024.json, written by
+    tests/golden/make_digests.py from the oracle alone)."""
+    import hashlib
+    import json
+    import os
+    from paper_2504_06182_gb300 import RR_BITS32
+
+    def sha(a):
+        return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
+    with open(os.path.join(os.path.dirname(__file__), "golden", "digests_1024.json")) as f:
+        gold = json.load(f)["bird"]
+    inst = gridgen.square_instance(0, 0, 1024, 0.6, 720)
+    st, mv = planner.plan(to_device(inst.grid, RR_BITS32), inst.rect, layout=RR_BITS32, n=1024, bird=True)
+    assert st == gold["status"] == 0
+    assert len(mv) == gold["n_moves"] and sha(mv.cpu().numpy()) == gold["moves_sha256"]
+    ops, mem = planner.batch(mv, 1024, 1024)
+    assert len(ops) == gold["n_ops"] and len(mem) == gold["n_members"]
+    assert sha(ops.cpu().numpy()) == gold["ops_sha256"]
+    assert sha(mem.cpu().numpy()) == gold["members_sha256"]
+
+
 def test_bird_served():
     """Served requests with RR_BIRD (waves of at most 5, three streams):
     every result equals the oracle's bird plan and its batches."""

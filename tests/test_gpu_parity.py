@@ -459,12 +459,18 @@ def test_batched_pipelined_every_config(planner):
 
 def test_grid_1024_bit_layout(planner):
     """Full-size 1024 x 1024 grid with a centred 720 x 720 target: the whole
-    move list against the oracle, and the batches against the oracle (all of
-    them with RR_FULL_PARITY=1, else a leading sample) plus the conservation
-    of elementary steps over all of them."""
+    move list against the oracle; every one of the 46.9 M batches and 76.3 M
+    members against the oracle's through the SHA-256 digests of its complete
+    output (tests/golden/digests_1024.json, written by
+    tests/golden/make_digests.py from the oracle alone), a leading sample
+    element by element (to locate a mismatch), and the conservation of
+    elementary steps."""
     from paper_2504_06182_gb300 import RR_BITS32
     inst = gridgen.square_instance(0, 0, 1024, 0.6, 720)
+    gold = load_digests()
+    assert list(inst.rect) == gold["rect"]
     ref = oracle.plan(inst.grid, inst.rect)
+    assert sha256_i32(ref.moves) == gold["redrec"]["moves_sha256"]      # the stored digests are this oracle's
     st, mv = gpu_plan(planner, inst.grid, inst.rect, RR_BITS32)
     assert st == 0 == ref.status
     assert (mv == ref.moves).all()
@@ -473,10 +479,21 @@ def test_grid_1024_bit_layout(planner):
     steps = int((np.abs(mv[:, 0] - mv[:, 2]) + np.abs(mv[:, 1] - mv[:, 3])).sum())
     assert len(mem) == steps == int(ops[:, 2].sum())
     assert (ops[:, 1] == np.concatenate([[0], np.cumsum(ops[:, 2])[:-1]])).all()
-    if os.environ.get("RR_FULL_PARITY") == "1":
-        rops, rmem = oracle.batch(ref.moves, 1024, 1024)
-        assert (ops == rops).all() and (mem == rmem).all()
-    else:
-        rops, rmem = oracle.batch(ref.moves, 1024, 1024, max_ops=200000)
-        assert (ops[: len(rops)] == rops).all()
-        assert (mem[: len(rmem)] == rmem).all()
+    rops, rmem = oracle.batch(ref.moves, 1024, 1024, max_ops=200000)
+    assert (ops[: len(rops)] == rops).all()
+    assert (mem[: len(rmem)] == rmem).all()
+    g = gold["redrec"]
+    assert len(ops) == g["n_ops"] and len(mem) == g["n_members"]
+    assert sha256_i32(ops) == g["ops_sha256"]
+    assert sha256_i32(mem) == g["members_sha256"]
+
+
+def load_digests():
+    import json
+    with open(os.path.join(os.path.dirname(__file__), "golden", "digests_1024.json")) as f:
+        return json.load(f)
+
+
+def sha256_i32(a) -> str:
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
