@@ -115,6 +115,26 @@ int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, int m, int n,
              rr_op *d_ops, int64_t cap_ops, int32_t *d_members, int64_t cap_members,
              int64_t *n_ops, int64_t *n_members, cudaStream_t stream);
 
+/* Plan one grid and, with RR_WITH_BATCH, batch its moves in ONE kernel
+ * launch: one block runs every stage of rr_plan (or rr_bird_plan with
+ * RR_BIRD) and of rr_batch in turn, with block barriers instead of kernel
+ * boundaries, no host round trip and one synchronisation. The paper's GPU
+ * red-rec is a single kernel for this reason (Sec. III.D): the latency of one
+ * reconfiguration cycle on one small grid, where launch gaps and host
+ * round trips would dominate the multi-kernel path. Sides up to
+ * RR_ONE_MAX_SIDE. flags: RR_WITH_BATCH, RR_BIRD, RR_STRICT_RESERVOIR (as
+ * rr_plan_mode). Outputs as rr_plan (moves) and, with RR_WITH_BATCH, as
+ * rr_batch (ops, members; ignored without it). counts (host, 4 entries):
+ * n_moves, n_steps (total elementary steps), n_ops, n_members. Returns
+ * RR_OK, RR_INFEASIBLE (no moves), RR_ERR_CAPACITY (the counts hold the
+ * required sizes: exact for moves; n_ops, n_members = n_steps for batches,
+ * an upper bound for n_ops) or an error. Results are bit-identical to
+ * rr_plan_mode followed by rr_batch. Synchronises `stream`. */
+#define RR_ONE_MAX_SIDE 256
+int rr_plan_one(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect, int flags,
+                rr_move *d_moves, int64_t cap_moves, rr_op *d_ops, int64_t cap_ops, int32_t *d_members,
+                int64_t cap_members, int64_t *counts, cudaStream_t stream);
+
 /* Many independent grids in one launch sequence (device-resident
  * descriptors). Inputs per instance: grid, layout, m, n, rect, output
  * pointers and capacities. Outputs per instance: status, n_moves, n_steps

@@ -67,9 +67,10 @@ class rr_serve_result(ctypes.Structure):
 
 
 EXPORTS = ("rr_ctx_create", "rr_ctx_destroy", "rr_plan", "rr_bird_plan", "rr_plan_mode", "rr_batch", "rr_plan_batched", "rr_set_tracing",
-           "rr_stage_times", "rr_launch_count", "rr_autotune", "rr_set_config", "rr_last_error", "rr_plan_noalloc", "rr_serve_open", "rr_serve_submit",
+           "rr_stage_times", "rr_launch_count", "rr_autotune", "rr_set_config", "rr_last_error", "rr_plan_noalloc", "rr_plan_one", "rr_serve_open", "rr_serve_submit",
            "rr_serve_poll", "rr_serve_release", "rr_serve_close")
 RR_NOALLOC_MAX_SIDE = 256
+RR_ONE_MAX_SIDE = 256
 
 _lib = None
 
@@ -110,6 +111,8 @@ def load(path: str = LIB_PATH):
     L.rr_set_config.restype = I32
     L.rr_plan_noalloc.argtypes = [P, I32, I32, I32, rr_rect, P, I64, ctypes.POINTER(I64), P]
     L.rr_plan_noalloc.restype = I32
+    L.rr_plan_one.argtypes = [P, P, I32, I32, I32, rr_rect, I32, P, I64, P, I64, P, I64, ctypes.POINTER(I64), P]
+    L.rr_plan_one.restype = I32
     L.rr_serve_open.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(rr_serve_config)]
     L.rr_serve_open.restype = I32
     L.rr_serve_submit.argtypes = [P, P, I32, I32, I32, rr_rect, ctypes.POINTER(I64)]
@@ -255,6 +258,17 @@ def rr_plan_noalloc(d_grid, layout, m, n, rect, d_moves, cap, stream=None):
     st = load().rr_plan_noalloc(_addr(d_grid), int(layout), int(m), int(n), rr_rect(*[int(v) for v in rect]),
                                 _addr(d_moves), int(cap), ctypes.byref(nm), _stream(stream))
     return st, nm.value
+
+
+def rr_plan_one(ctx, d_grid, layout, m, n, rect, flags, d_moves, cap_moves, d_ops=None, cap_ops=0, d_members=None,
+                cap_members=0, stream=None):
+    """Plan (and with RR_WITH_BATCH batch) one grid in one kernel launch.
+    Returns (status, n_moves, n_steps, n_ops, n_members)."""
+    counts = (ctypes.c_int64 * 4)()
+    st = load().rr_plan_one(ctx, _addr(d_grid), int(layout), int(m), int(n), rr_rect(*[int(v) for v in rect]),
+                            int(flags), _addr(d_moves), int(cap_moves), _addr(d_ops), int(cap_ops), _addr(d_members),
+                            int(cap_members), counts, _stream(stream))
+    return (st, *[int(c) for c in counts])
 
 
 # ------------------------------------------------------------------ serving

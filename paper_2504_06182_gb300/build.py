@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "librr.so")
-SOURCES = ["rr_plan.cu", "rr_bird.cu", "rr_batch.cu", "rr_capi.cu", "rr_noalloc.cu", "rr_serve.cu"]
+SOURCES = ["rr_plan.cu", "rr_bird.cu", "rr_batch.cu", "rr_one.cu", "rr_capi.cu", "rr_noalloc.cu", "rr_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -47,7 +47,7 @@ static_assert(sizeof(rr_instance) == 128, "rr_instance layout is part of the ABI
 static constexpr int SMALL_CALL = 8;
 
 // Kernels launched with more than the default 48 KB of dynamic shared memory.
-enum { SM_GSORT, SM_GSWEEP_H, SM_GSWEEP_V, SM_SIM16, SM_SIM32, SM_SIM16W, SM_SIM32W, SM_BIRD, SM_NKERNEL };
+enum { SM_GSORT, SM_GSWEEP_H, SM_GSWEEP_V, SM_SIM16, SM_SIM32, SM_SIM16W, SM_SIM32W, SM_BIRD, SM_ONE, SM_NKERNEL };
 
 struct rr_ctx {
     int device;
@@ -56,6 +56,8 @@ struct rr_ctx {
     unsigned long long arena_size;
     unsigned long long *d_top;
     rr_instance *d_one;       // descriptor slot of the single-grid entry points
+    rr_instance *h_one;       // rr_plan_one: the final descriptor, written by the kernel (mapped host memory)
+    rr_instance *d_hone;      // its device address
     JobWS *d_ws;
     int ws_cap;
     char err[256];
@@ -141,7 +143,7 @@ static int smem_limits(int dev, int *out)
         cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         const void *fn[SM_NKERNEL] = {(const void *)k_gsort, (const void *)k_gsweep_h, (const void *)k_gsweep_v,
                                       (const void *)k_sim16, (const void *)k_sim32, (const void *)k_sim16w,
-                                      (const void *)k_sim32w, (const void *)k_bird};
+                                      (const void *)k_sim32w, (const void *)k_bird, one_kernel()};
         for (int i = 0; e == cudaSuccess && i < SM_NKERNEL; ++i) {
             cudaFuncAttributes fa;
             e = cudaFuncGetAttributes(&fa, fn[i]);
@@ -201,11 +203,14 @@ extern "C" int rr_ctx_create(rr_ctx **out, int64_t arena_bytes)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->arena, (size_t)arena_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_top, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_one, sizeof(rr_instance));
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&ctx->h_one, sizeof(rr_instance), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&ctx->d_hone, ctx->h_one, 0);
     if (e != cudaSuccess) {
         fail(nullptr, RR_ERR_CUDA, "rr_ctx_create: %s", cudaGetErrorString(e));
         if (ctx->arena) cudaFree(ctx->arena);
         if (ctx->d_top) cudaFree(ctx->d_top);
         if (ctx->d_one) cudaFree(ctx->d_one);
+        if (ctx->h_one) cudaFreeHost(ctx->h_one);
         delete ctx;
         return RR_ERR_CUDA;
     }
@@ -247,6 +252,7 @@ extern "C" int rr_ctx_destroy(rr_ctx *ctx)
     cudaFree(ctx->arena);
     cudaFree(ctx->d_top);
     cudaFree(ctx->d_one);
+    if (ctx->h_one) cudaFreeHost(ctx->h_one);
     cudaFree(ctx->d_ws);
     drop_graph(ctx);
     if (ctx->capStream) cudaStreamDestroy(ctx->capStream);
@@ -530,6 +536,44 @@ extern "C" int rr_batch(rr_ctx *ctx, const rr_move *d_moves, int64_t n_moves, in
     *n_members = h.n_members;
     if (h.status < 0) return fail(ctx, h.status, "rr_batch: device status %d", h.status);
     return h.status;
+}
+
+extern "C" int rr_plan_one(rr_ctx *ctx, const void *d_grid, int layout, int m, int n, rr_rect rect, int flags,
+                           rr_move *d_moves, int64_t cap_moves, rr_op *d_ops, int64_t cap_ops, int32_t *d_members,
+                           int64_t cap_members, int64_t *counts, cudaStream_t stream)
+{
+    const bool batch = (flags & RR_WITH_BATCH) != 0;
+    if (!ctx || !d_grid || !counts || (layout != RR_U8 && layout != RR_BITS32) || !rect_ok(m, n, rect) ||
+        m > ONE_MAX_SIDE || n > ONE_MAX_SIDE || cap_moves < 0 || (cap_moves > 0 && !d_moves) ||
+        (flags & ~(RR_WITH_BATCH | RR_BIRD | RR_STRICT_RESERVOIR)) ||
+        (batch && (cap_ops < 0 || cap_members < 0 || (cap_ops > 0 && !d_ops) || (cap_members > 0 && !d_members))))
+        return fail(ctx, RR_ERR_ARG, "rr_plan_one: bad argument (m=%d n=%d rect=[%d,%d,%d,%d] layout=%d flags=%d)",
+                    m, n, rect.r0, rect.c0, rect.r1, rect.c1, layout, flags);
+    const int side = std::max(m, n);
+    const size_t smem = one_smem_bytes(side, flags);
+    if (smem > (size_t)ctx->smemLimit[SM_ONE])
+        return fail(ctx, RR_ERR_ARG, "rr_plan_one: shared memory %zu for side %d too large", smem, side);
+    rr_instance h;
+    std::memset(&h, 0, sizeof(h));
+    h.grid = d_grid; h.layout = layout; h.m = m; h.n = n; h.rect = rect;
+    h.moves = d_moves; h.cap_moves = cap_moves;
+    if (batch) { h.ops = d_ops; h.cap_ops = cap_ops; h.members = d_members; h.cap_members = cap_members; }
+    ctx->nmarks = 0;
+    mark(ctx, stream, "k_one");
+    if (one_launch(h, ctx->d_one, ctx->d_ws, arena_of(ctx), flags, side, smem, ctx->d_hone, stream) != RR_OK)
+        return fail(ctx, RR_ERR_CUDA, "rr_plan_one: launch: %s", cudaGetErrorString(cudaGetLastError()));
+    mark(ctx, stream, nullptr);
+    ctx->nlaunch += 1;
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    const volatile rr_instance *r = ctx->h_one;
+    counts[0] = r->n_moves;
+    counts[1] = r->n_steps;
+    counts[2] = batch ? r->n_ops : 0;
+    counts[3] = batch ? r->n_members : 0;
+    const int st = r->status;
+    if (st < 0 && st != RR_ERR_CAPACITY)
+        return fail(ctx, st, "rr_plan_one: device status %d (n_moves=%lld)", st, (long long)counts[0]);
+    return st;
 }
 
 // Calls over at least this many grids, with batching, may run pipelined.

@@ -9,6 +9,14 @@ namespace rrk {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Block coordinates of a stage (the stage functions of rr_plan.cuh,
+// rr_bird.cuh and rr_batch.cuh): the hardware's when a stage runs as a
+// kernel of its own; x = 0, gx = 1 when one block runs the whole path of one
+// grid (the single-grid kernel), so that every grid-stride loop covers all
+// of its items.
+struct Blk { int x, y, gx; };
+__device__ __forceinline__ Blk hw_blk() { return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x}; }
+
 // Column classification after the column phase (Alg. 1 first loop, solved for
 // every column of non-negative surplus at once as in Sec. III.D).
 enum ColKind : int32_t {
@@ -240,5 +248,16 @@ __device__ __forceinline__ int band_P(const int16_t *hr, int nh, int nband, int 
 
 } // namespace rrk
 
-// Library-internal hook between translation units (not part of the C ABI).
+// Library-internal hooks between translation units (not part of the C ABI).
 int rr_internal_reserve(rr_ctx *ctx, int count);
+
+namespace rrk {
+// The single-grid kernel (rr_one.cu): one block of ONE_THREADS threads runs
+// planning, Gamma and batching of one grid with sides up to ONE_MAX_SIDE.
+constexpr int ONE_THREADS = 256;
+constexpr int ONE_MAX_SIDE = 256;
+size_t one_smem_bytes(int side, int flags);
+const void *one_kernel();
+int one_launch(rr_instance h, rr_instance *d_inst, JobWS *d_ws, Arena A, int flags, int side, size_t smem,
+               rr_instance *hostOut, cudaStream_t s);
+} // namespace rrk

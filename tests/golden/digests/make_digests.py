@@ -1,4 +1,4 @@
-"""Writes tests/golden/digests_1024.json: SHA-256 digests of the oracle's
+"""Writes tests/golden/digests/oracle_1024.json: SHA-256 digests of the oracle's
 complete outputs on the 1024 x 1024 workload (fill 0.6, centred 720 x 720
 target, seed 0, grid 0), for outputs too large to recompute inside a test.
 
@@ -9,7 +9,7 @@ order: moves (k, 4) = (src_row, src_col, dst_row, dst_col); ops (b, 3) =
 oracle about ten minutes on one core (46.9 M batches, Alg. 4 taken
 literally); the bird plan about as long again.
 
-    python tests/golden/make_digests.py [--no-bird]
+    python tests/golden/digests/make_digests.py [--no-bird]
 """
 from __future__ import annotations
 
@@ -22,14 +22,14 @@ import time
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(os.path.dirname(HERE))
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(HERE)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 import gridgen  # noqa: E402
 import oracle  # noqa: E402
 
-OUT = os.path.join(HERE, "digests_1024.json")
+OUT = os.path.join(HERE, "oracle_1024.json")
 
 
 def sha(a: np.ndarray) -> str:
@@ -57,7 +57,7 @@ def main():
         "workload": "1024 x 1024, Bernoulli(0.6) from gridgen.square_instance(seed 0, grid 0), "
                     "centred 720 x 720 target",
         "rect": list(inst.rect),
-        "written_by": "tests/golden/make_digests.py (oracle only)",
+        "written_by": "tests/golden/digests/make_digests.py (oracle only)",
     }
     out["redrec"] = entry(oracle.plan(inst.grid, inst.rect), 1024, 1024)
     print("red-rec", out["redrec"], flush=True)

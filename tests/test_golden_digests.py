@@ -1,5 +1,5 @@
 """The stored digests of the oracle's complete 1024 x 1024 outputs
-(tests/golden/digests_1024.json) belong to the oracle as it stands: the
+(tests/golden/digests/oracle_1024.json) belong to the oracle as it stands: the
 red-rec move list is replanned here and hashed (the batch digests take the
 oracle minutes and are checked against the GPU in the -m gpu tests), and the
 counts are consistent with the moves they describe."""
@@ -14,7 +14,7 @@ import oracle
 
 
 def _gold():
-    with open(os.path.join(os.path.dirname(__file__), "golden", "digests_1024.json")) as f:
+    with open(os.path.join(os.path.dirname(__file__), "golden", "digests", "oracle_1024.json")) as f:
         return json.load(f)
 
 

@@ -197,8 +197,8 @@ def test_bird_grid_1024_replay(planner):
 def test_bird_grid_1024_full_digest(planner):
     """The same 1024 x 1024 grid: the GPU's complete bird plan and all of its
     batches (85.7 M of them) against the SHA-256 digests of the oracle's
-    complete outputs (tests/golden/digests_1024.json, written by
-    tests/golden/make_digests.py from the oracle alone)."""
+    complete outputs (tests/golden/digests/oracle_1024.json, written by
+    tests/golden/digests/make_digests.py from the oracle alone)."""
     import hashlib
     import json
     import os
@@ -206,7 +206,7 @@ def test_bird_grid_1024_full_digest(planner):
 
     def sha(a):
         return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
-    with open(os.path.join(os.path.dirname(__file__), "golden", "digests_1024.json")) as f:
+    with open(os.path.join(os.path.dirname(__file__), "golden", "digests", "oracle_1024.json")) as f:
         gold = json.load(f)["bird"]
     inst = gridgen.square_instance(0, 0, 1024, 0.6, 720)
     st, mv = planner.plan(to_device(inst.grid, RR_BITS32), inst.rect, layout=RR_BITS32, n=1024, bird=True)

@@ -461,8 +461,8 @@ def test_grid_1024_bit_layout(planner):
     """Full-size 1024 x 1024 grid with a centred 720 x 720 target: the whole
     move list against the oracle; every one of the 46.9 M batches and 76.3 M
     members against the oracle's through the SHA-256 digests of its complete
-    output (tests/golden/digests_1024.json, written by
-    tests/golden/make_digests.py from the oracle alone), a leading sample
+    output (tests/golden/digests/oracle_1024.json, written by
+    tests/golden/digests/make_digests.py from the oracle alone), a leading sample
     element by element (to locate a mismatch), and the conservation of
     elementary steps."""
     from paper_2504_06182_gb300 import RR_BITS32
@@ -490,7 +490,7 @@ def test_grid_1024_bit_layout(planner):
 
 def load_digests():
     import json
-    with open(os.path.join(os.path.dirname(__file__), "golden", "digests_1024.json")) as f:
+    with open(os.path.join(os.path.dirname(__file__), "golden", "digests", "oracle_1024.json")) as f:
         return json.load(f)
 
 
