@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=1000,
                     help="requests of the served high-load run (0: skip the served runs)")
     ap.add_argument("--served-load", type=float, default=0.8, help="arrival rate as a fraction of saturation")
+    ap.add_argument("--served-plain-requests", type=int, default=48,
+                    help="requests per arrival rate at fractions of the plain path's rate")
     ap.add_argument("--no-bird", action="store_true", help="skip the bird planner's line")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch configuration (for profiling fixed launches)")
@@ -178,22 +180,48 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "k_sim_traffic.json")
+TRAFFIC_SOURCES = ("rr_batch.cuh", "rr_batch.cu", "rr_internal.cuh")
+
+
+def sources_fingerprint():
+    """First 16 hex digits of sha256 over the simulation kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2504_06182_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def measured_traffic_ratio(kernel):
     """DRAM bytes per algorithmic byte of `kernel` from the committed ncu
-    summary, or None when there is none or the kernel sources changed since."""
-    import hashlib
-    import re
+    record (profiles/k_sim_traffic.json), or None when there is none or the
+    kernel's sources changed since it was taken."""
     try:
-        text = open(os.path.join(ROOT, "profiles", "k_sim_mixed256.md")).read()
-        rec = json.loads(re.search(r"<!-- traffic: (\{.*?\}) -->", text).group(1))
-        h = hashlib.sha256()
-        for f in ("rr_batch.cu", "rr_internal.cuh"):
-            h.update(open(os.path.join(ROOT, "paper_2504_06182_gb300", "csrc", f), "rb").read())
+        rec = json.load(open(TRAFFIC_JSON))
+        fp = sources_fingerprint()
     except Exception:
         return None
-    if rec.get("kernel") != kernel or h.hexdigest()[:16] != rec.get("src_sha256_16"):
+    if rec.get("kernel") != kernel or fp != rec.get("src_sha256_16"):
         return None
     return float(rec["ratio"])
+
+
+def nb_alpha(ops, members):
+    """Batched transfer operations of one grid's batch list (Sec. V, control
+    operations): a batch in which some token takes its first elementary step
+    needs one parallel extraction, a batch in which some token takes its last
+    step one parallel implantation; NB_alpha counts both kinds of batches.
+    ops (b, 3) = (dir, first, count), members (s,) move ids, in batch order."""
+    ops = np.asarray(ops).reshape(-1, 3)
+    members = np.asarray(members).reshape(-1)
+    if len(members) == 0:
+        return 0
+    bidx = np.repeat(np.arange(len(ops)), ops[:, 2])
+    _, first = np.unique(members, return_index=True)
+    _, last_rev = np.unique(members[::-1], return_index=True)
+    last = len(members) - 1 - last_rev
+    return int(len(np.unique(bidx[first])) + len(np.unique(bidx[last])))
 
 
 # ------------------------------------------------------------- paper geometry
@@ -292,8 +320,11 @@ def make_entries(rr, insts, grids, offs, sides, moves=None, ops=None, mem=None, 
 
 def sized_descriptors(rr, P, insts, grids, offs, sides, extra_flags=0):
     """Sizes every grid's outputs on the device (a planning pass without
-    output room gives the move counts, a planning + batching pass the step
-    counts), allocates them and returns (descriptors, moves, ops, members)."""
+    output room gives the move counts, a planning + batching pass with room
+    for one batch per elementary step the exact step and batch counts),
+    allocates them packed back to back, exactly, and returns (descriptors,
+    moves, ops, members, layout); layout holds the per-grid counts and
+    offsets into the packed buffers."""
     import torch
     from paper_2504_06182_gb300.planner import pack_instances, unpack_instances
     count, max_side, dev = len(insts), max(sides), grids.device
@@ -314,7 +345,31 @@ def sized_descriptors(rr, P, insts, grids, offs, sides, extra_flags=0):
     caps = [(int(n_moves[g]), int(n_steps[g]), int(n_steps[g]), int(mo[g]), int(so[g]), int(so[g]))
             for g in range(count)]
     d_inst = pack_instances(make_entries(rr, insts, grids, offs, sides, moves, ops, mem, caps))
-    return d_inst, moves, ops, mem
+    rr.rr_plan_batched(P.ctx, d_inst, count, max_side, rr.RR_WITH_BATCH | extra_flags)
+    torch.cuda.synchronize()
+    res = unpack_instances(d_inst, count)
+    n_ops = np.array([x.n_ops if x.status == rr.RR_OK else 0 for x in res], dtype=np.int64)
+    del ops
+    oo = np.concatenate([[0], np.cumsum(n_ops)])
+    ops = torch.empty((int(n_ops.sum()) + 1, 3), dtype=torch.int32, device=dev)
+    caps = [(int(n_moves[g]), int(n_ops[g]), int(n_steps[g]), int(mo[g]), int(oo[g]), int(so[g]))
+            for g in range(count)]
+    d_inst = pack_instances(make_entries(rr, insts, grids, offs, sides, moves, ops, mem, caps))
+    lay = {"n_moves": n_moves, "n_ops": n_ops, "n_steps": n_steps, "mo": mo, "oo": oo, "so": so}
+    return d_inst, moves, ops, mem, lay
+
+
+def nb_alpha_sample(insts, lay, ops_of, mem_of, limit=256):
+    """Mean NB_alpha over the first `limit` feasible grids (ops_of(g) and
+    mem_of(g) give that grid's host arrays)."""
+    vals = []
+    for g in range(len(insts)):
+        if len(vals) >= limit:
+            break
+        if lay["n_steps"][g] == 0 or lay["n_ops"][g] == 0:
+            continue
+        vals.append(nb_alpha(ops_of(g), mem_of(g)))
+    return (float(np.mean(vals)) if vals else None), len(vals)
 
 
 def run_bird(args, rr, P, insts, grids, offs, sides, flush, cpu_threads):
@@ -327,7 +382,7 @@ def run_bird(args, rr, P, insts, grids, offs, sides, flush, cpu_threads):
     from paper_2504_06182_gb300.planner import unpack_instances
     count, max_side = len(insts), max(sides)
     flags = rr.RR_WITH_BATCH | rr.RR_BIRD
-    d_inst, moves, ops, mem = sized_descriptors(rr, P, insts, grids, offs, sides, rr.RR_BIRD)
+    d_inst, moves, ops, mem, lay = sized_descriptors(rr, P, insts, grids, offs, sides, rr.RR_BIRD)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         rr.rr_plan_batched(P.ctx, d_inst, count, max_side, flags, stream)
@@ -355,6 +410,9 @@ def run_bird(args, rr, P, insts, grids, offs, sides, flush, cpu_threads):
     tot_moves = sum(x.n_moves for x in res)
     tot_ops = sum(x.n_ops for x in res)
     tot_mem = sum(x.n_members for x in res)
+    nba, nba_n = nb_alpha_sample(
+        insts, lay, lambda g: ops[lay["oo"][g]:lay["oo"][g + 1]].cpu().numpy(),
+        lambda g: mem[lay["so"][g]:lay["so"][g] + lay["n_steps"][g]].cpu().numpy())
     del moves, ops, mem
     cpu = None
     if not args.no_cpu_baseline:
@@ -369,7 +427,8 @@ def run_bird(args, rr, P, insts, grids, offs, sides, flush, cpu_threads):
             "stages_ms_per_step": {k: v / args.steps for k, v in sorted(stage_tot.items(), key=lambda kv: -kv[1])},
             "control_ops_per_feasible_grid": {
                 "N_nu": tot_mem / max(1, feasible), "N_alpha": 2 * tot_moves / max(1, feasible),
-                "NB_nu": tot_ops / max(1, feasible), "N_nu_per_NB_nu": tot_mem / max(1, tot_ops)},
+                "NB_nu": tot_ops / max(1, feasible), "N_nu_per_NB_nu": tot_mem / max(1, tot_ops),
+                "NB_alpha": nba, "NB_alpha_sample": f"first {nba_n} feasible grids"},
             "feasible": int(feasible), "cpu_baseline": cpu}
 
 
@@ -413,36 +472,56 @@ def fifo_latencies(arrivals, service):
     return out
 
 
+def served_grid(seed, i):
+    """Request i of the served stream: (packed grid words, target rect, side)."""
+    side, _ = gridgen.mixed_draw(seed, i, SERVED_SIDES, 0.6, 0.6)
+    inst = gridgen.square_instance(seed, i, side, 0.6)
+    return np.ascontiguousarray(gridgen.pack_bits32(inst.grid).view(np.int32)), inst.rect, side
+
+
+def _served_chunk(job):
+    seed, lo, hi = job
+    return [served_grid(seed, i) for i in range(lo, hi)]
+
+
+def served_grids(seed, n):
+    """The first n requests' grids, each drawn from its own seeded stream
+    (large counts on a spawned process pool: CUDA is already initialised)."""
+    if n <= 2000:
+        return [served_grid(seed, i) for i in range(n)]
+    import multiprocessing as mp
+    jobs = [(seed, lo, min(n, lo + 500)) for lo in range(0, n, 500)]
+    with mp.get_context("spawn").Pool(os.cpu_count() or 4) as pool:
+        parts = pool.map(_served_chunk, jobs)
+    return [x for part in parts for x in part]
+
+
 def run_served(rr, requests, load, seed=5, slots=256, streams=32, max_wave=8, plain_n=48, lam_n=48):
     """Served stream (C5): grids with side uniform in {64, 80, ..., 512},
     p = 0.6, centred floor(0.7 side) target, submitted from host memory;
-    latency = completion - submission per request.
+    latency = completion - submission per request. Every request of the
+    high-load run is a distinct seeded grid.
 
-    1. plain: the first plain_n pool grids one at a time (H2D of the grid,
+    1. plain: the first plain_n grids one at a time (H2D of the grid,
        rr_plan, rr_batch, synchronise): its maximum rate and service times;
     2. Poisson arrivals at 0.5, 0.8 and 0.95 x that rate (lam_n requests
-       each, cycling through those grids): served p50/p99, and plain p50/p99
-       for the same arrivals from a first-in-first-out queue over the
-       measured service times;
-    3. saturation: a burst of the pool's requests at once;
+       each, distinct grids): served p50/p99, and plain p50/p99 for the same
+       arrivals from a first-in-first-out queue over the measured service
+       times (cycled over the plain_n sampled grids);
+    3. saturation: a burst of 192 requests at once;
     4. Poisson arrivals at `load` x the served saturation (`requests`)."""
     import torch
     from paper_2504_06182_gb300.planner import Planner
-    pool = []
-    for g in range(256):
-        side, _ = gridgen.mixed_draw(seed, g, SERVED_SIDES, 0.6, 0.6)
-        inst = gridgen.square_instance(seed, g, side, 0.6)
-        pool.append((np.ascontiguousarray(gridgen.pack_bits32(inst.grid).view(np.int32)), inst))
+    pool = served_grids(seed, max(requests, plain_n, lam_n, 192))
 
     # 1. plain, one grid per call
     P = Planner(arena_bytes=2 << 30)
     service = []
     try:
-        for w, inst in pool[:1] + pool[:plain_n]:          # the first call warms up
-            s_ = inst.grid.shape[0]
+        for w, rect, s_ in pool[:1] + pool[:plain_n]:          # the first call warms up
             t0 = time.perf_counter()
             g = torch.from_numpy(w).cuda()
-            st, mv = P.plan(g, inst.rect, layout=rr.RR_BITS32, n=s_, cap=2 * s_ * s_)
+            st, mv = P.plan(g, rect, layout=rr.RR_BITS32, n=s_, cap=2 * s_ * s_)
             if st == rr.RR_OK and len(mv):
                 P.batch(mv, s_, s_)
             torch.cuda.synchronize()
@@ -458,8 +537,8 @@ def run_served(rr, requests, load, seed=5, slots=256, streams=32, max_wave=8, pl
                            arena_bytes=arena, heap_bytes=24 << 30)
     try:
         def submit(i):
-            w, inst = pool[i % len(pool)]
-            st, t = rr.rr_serve_submit(srv, w, rr.RR_BITS32, inst.grid.shape[0], inst.grid.shape[1], inst.rect)
+            w, rect, s_ = pool[i % len(pool)]
+            st, t = rr.rr_serve_submit(srv, w, rr.RR_BITS32, s_, s_, rect)
             if st != rr.RR_OK:
                 raise rr.RRError(st, "rr_serve_submit")
             return t
@@ -500,7 +579,7 @@ def run_served(rr, requests, load, seed=5, slots=256, streams=32, max_wave=8, pl
         vs_plain = []
         for k, frac in enumerate((0.5, 0.8, 0.95)):
             rate = frac * plain_rate
-            arrivals, lat, _ = poisson(rate, lam_n, lambda i: i % plain_n, seed + 10 + k)
+            arrivals, lat, _ = poisson(rate, lam_n, lambda i: i, seed + 10 + k)
             plat = np.array(fifo_latencies(arrivals, [service[i % plain_n] for i in range(lam_n)])) * 1e3
             vs_plain.append({"rate_per_s": rate, "fraction_of_plain_max": frac, "requests": lam_n,
                              "served_p50_ms": float(np.percentile(lat, 50)),
@@ -508,7 +587,7 @@ def run_served(rr, requests, load, seed=5, slots=256, streams=32, max_wave=8, pl
                              "plain_p50_ms": float(np.percentile(plat, 50)),
                              "plain_p99_ms": float(np.percentile(plat, 99))})
         # 3. saturation throughput: a burst of the pool's requests at once
-        nb = min(len(pool), 192)
+        nb = 192
         t0 = time.perf_counter()
         out = [submit(i) for i in range(nb)]
         drain(out, [], True)
@@ -517,13 +596,13 @@ def run_served(rr, requests, load, seed=5, slots=256, streams=32, max_wave=8, pl
         _, lat, gps = poisson(load * sat, requests, lambda i: i, seed)
         return {"sides": "64..512 step 16", "p": 0.6,
                 "server": {"slots": slots, "streams": streams, "max_wave": max_wave},
-                "plain_grids_per_s": plain_rate, "plain_sample": f"first {plain_n} pool grids, one call each",
+                "plain_grids_per_s": plain_rate, "plain_sample": f"first {plain_n} grids, one call each",
                 "saturation_grids_per_s": sat,
                 "at_fraction_of_plain": vs_plain,
                 "high_load": {"rate_per_s": load * sat, "fraction_of_saturation": load, "requests": requests,
                               "grids_per_s": gps, "p50_ms": float(np.percentile(lat, 50)),
                               "p99_ms": float(np.percentile(lat, 99))},
-                "note": f"requests cycle through {len(pool)} distinct seeded grids"}
+                "note": f"{len(pool)} distinct seeded grids, request i is grid i"}
     finally:
         rr.rr_serve_close(srv)
 
@@ -563,7 +642,7 @@ def run_ours(args, rank, world, local):
     max_side = max(sides)
 
     P = Planner(arena_bytes=int(os.environ.get("RR_ARENA_GB", "24")) << 30)
-    d_inst, moves, ops, mem = sized_descriptors(rr, P, insts, grids, offs, sides)
+    d_inst, moves, ops, mem, lay = sized_descriptors(rr, P, insts, grids, offs, sides)
     inst_host = d_inst.cpu().pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
@@ -637,11 +716,17 @@ def run_ours(args, rank, world, local):
     feasible = sum(x.status == rr.RR_OK for x in res)
 
     # end to end through the public call with host buffers: H2D of the packed
-    # grids and descriptors, the planning call, D2H of the per-grid results
+    # grids and descriptors, the planning call, D2H of the results: the
+    # per-grid descriptors (statuses and counts) and every move, batch and
+    # batch member, packed exactly (what drives the tweezers)
     e2e_ms = []
-    h2d = host.numel() * 4 + inst_host.numel()
-    d2h = inst_host.numel()
+    nm_, no_, ns_ = int(lay["n_moves"].sum()), int(lay["n_ops"].sum()), int(lay["n_steps"].sum())
     back = torch.empty_like(inst_host).pin_memory()
+    moves_h = torch.empty((nm_, 4), dtype=torch.int32, pin_memory=True)
+    ops_h = torch.empty((no_, 3), dtype=torch.int32, pin_memory=True)
+    mem_h = torch.empty((ns_,), dtype=torch.int32, pin_memory=True)
+    h2d = host.numel() * 4 + inst_host.numel()
+    d2h = inst_host.numel() + 4 * (moves_h.numel() + ops_h.numel() + mem_h.numel())
     for _ in range(args.steps):
         flush.fill_(1)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -650,10 +735,17 @@ def run_ours(args, rank, world, local):
         d_inst.copy_(inst_host, non_blocking=True)
         step()
         back.copy_(d_inst, non_blocking=True)
+        moves_h.copy_(moves[:nm_], non_blocking=True)
+        ops_h.copy_(ops[:no_], non_blocking=True)
+        mem_h.copy_(mem[:ns_], non_blocking=True)
         b.record(stream)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e_total = max_over_ranks(sum(e2e_ms), dev, world)
+    ops_np, mem_np = ops_h.numpy(), mem_h.numpy()
+    nba, nba_n = nb_alpha_sample(insts, lay, lambda g: ops_np[lay["oo"][g]:lay["oo"][g + 1]],
+                                 lambda g: mem_np[lay["so"][g]:lay["so"][g] + lay["n_steps"][g]])
+    del moves_h, ops_h, mem_h, ops_np, mem_np
 
     if rank != 0:
         if world > 1:
@@ -669,7 +761,8 @@ def run_ours(args, rank, world, local):
         if not args.no_bird else None
     P.close()
     torch.cuda.empty_cache()
-    served = run_served(rr, args.served_requests, args.served_load) if args.served_requests > 0 else None
+    served = run_served(rr, args.served_requests, args.served_load, plain_n=min(48, args.served_plain_requests),
+                        lam_n=args.served_plain_requests) if args.served_requests > 0 else None
 
     peaks = {}
     try:
@@ -711,7 +804,9 @@ def run_ours(args, rank, world, local):
                                                                "block_budget_scale": 2.0 ** tuned_shift,
                                  "largest_first": ["off", "1/4", "1/16, 1/4", "1/16, 1/8, 1/4, 1/2", "1/64, 1/16, 1/4"][tuned_pipe]}},
         "e2e": {"value": count * world * args.steps / (e2e_total * 1e-3), "unit": "grids/s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "note": "H2D of the packed grids and descriptors, the call, D2H of the descriptors and of "
+                        "every move, batch and member (pinned host buffers), per step"},
         "gpu_launches": launches,
         "graph": {"value": count * args.steps / (graph_total * 1e-3), "unit": "grids/s",
                   "note": "same step replayed from one captured CUDA graph (RR_GRAPH), inputs resident"},
@@ -728,10 +823,13 @@ def run_ours(args, rank, world, local):
         # control operations of one reconfiguration cycle (§V): displacement
         # operations N_nu = elementary steps, transfer operations N_alpha = one
         # extraction and one implantation per move, batched displacement
-        # sequences NB_nu = batches (the paper defines no batching of transfers)
+        # sequences NB_nu = batches, batched transfers NB_alpha = batches with
+        # a first step (one parallel extraction) plus batches with a last step
+        # (one parallel implantation), on a sample of the grids
         "control_ops_per_feasible_grid": {
             "N_nu": tot_mem / max(1, feasible), "N_alpha": 2 * tot_moves / max(1, feasible),
-            "NB_nu": tot_ops / max(1, feasible), "N_nu_per_NB_nu": tot_mem / max(1, tot_ops)},
+            "NB_nu": tot_ops / max(1, feasible), "N_nu_per_NB_nu": tot_mem / max(1, tot_ops),
+            "NB_alpha": nba, "NB_alpha_sample": f"first {nba_n} feasible grids"},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -825,11 +923,30 @@ def run_configs(args):
     for name, side, t, lay in SINGLE_CONFIGS:
         layout = rr.RR_U8 if lay == "u8" else rr.RR_BITS32
         plan_us, both_us, bird_us, outs = [], [], [], None
+        one_plan_us, one_both_us = [], []
         for sd in seeds:
             inst = gridgen.square_instance(sd, 0, side, 0.6, t)
             host = inst.grid if lay == "u8" else gridgen.pack_bits32(inst.grid).view(np.int32)
             g = torch.from_numpy(np.ascontiguousarray(host)).cuda()
             cap = 2 * side * side
+            if side <= rr.RR_ONE_MAX_SIDE:
+                # the one-launch path, outputs sized beforehand (a real-time
+                # loop keeps its buffers): plan, and plan + batching
+                st, mv = P.plan(g, inst.rect, layout=layout, n=side, cap=cap)
+                k = max(1, len(mv))
+                nst = max(1, path_steps(mv.cpu().numpy())) if len(mv) else 1
+                o_mv = torch.empty((k, 4), dtype=torch.int32, device="cuda")
+                o_ops = torch.empty((nst, 3), dtype=torch.int32, device="cuda")
+                o_mem = torch.empty((nst,), dtype=torch.int32, device="cuda")
+
+                def one(flags):
+                    r = rr.rr_plan_one(P.ctx, g, layout, side, side, inst.rect, flags, o_mv, k, o_ops, nst, o_mem, nst)
+                    if r[0] not in (rr.RR_OK, rr.RR_INFEASIBLE):
+                        raise rr.RRError(r[0], rr.rr_last_error(P.ctx))
+                    return r
+                one(rr.RR_WITH_BATCH)
+                one_plan_us.append(median_us(lambda: one(0), 20))
+                one_both_us.append(median_us(lambda: one(rr.RR_WITH_BATCH), 20 if side <= 64 else 3))
 
             def plan():
                 r = P.plan(g, inst.rect, layout=layout, n=side, cap=cap)
@@ -859,6 +976,10 @@ def run_configs(args):
                 "gpu": {"plan_us": float(np.median(plan_us)), "plan_batch_us": float(np.median(both_us)),
                         "bird_plan_us": float(np.median(bird_us)),
                         "path": "one rr_plan (and rr_batch) call per grid, grid resident on the device, synchronised"},
+                "gpu_one_launch": {"plan_us": float(np.median(one_plan_us)),
+                                   "plan_batch_us": float(np.median(one_both_us)),
+                                   "path": "one rr_plan_one call (a single kernel launch) per grid, outputs "
+                                           "allocated beforehand, synchronised"} if one_plan_us else None,
                 "cpu_baseline": cpu[side], "seed0_outputs": outs, "data": "synthetic"}
         print(json.dumps(line), flush=True)
     run_chains(rr, P, cpu_chain)

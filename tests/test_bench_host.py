@@ -1,10 +1,9 @@
 """Host-side logic of bench.py (no GPU): the plain path's queueing model, the
-traffic ratio read from the committed ncu summary, the workload constructors
-and the per-rank seeds."""
+traffic ratio read from the committed ncu record, the batched-transfer count,
+the workload constructors and the per-rank seeds."""
 import hashlib
 import json
 import os
-import re
 
 import numpy as np
 
@@ -32,15 +31,47 @@ def test_fifo_latencies_single_server():
 
 def test_traffic_ratio_tracks_the_sources():
     """The ratio is reported only for the profiled kernel and only while the
-    sources hashed in the summary are unchanged."""
-    text = open(os.path.join(bench.ROOT, "profiles", "k_sim_mixed256.md")).read()
-    rec = json.loads(re.search(r"<!-- traffic: (\{.*?\}) -->", text).group(1))
+    sources fingerprinted in the record are unchanged."""
+    rec = json.load(open(bench.TRAFFIC_JSON))
     h = hashlib.sha256()
-    for f in ("rr_batch.cu", "rr_internal.cuh"):
+    for f in ("rr_batch.cuh", "rr_batch.cu", "rr_internal.cuh"):
         h.update(open(os.path.join(bench.ROOT, "paper_2504_06182_gb300", "csrc", f), "rb").read())
     expect = float(rec["ratio"]) if h.hexdigest()[:16] == rec["src_sha256_16"] else None
     assert bench.measured_traffic_ratio("k_sim") == expect
     assert bench.measured_traffic_ratio("k_bsort") is None
+    assert bench.sources_fingerprint() == h.hexdigest()[:16]
+
+
+def _fixture(name):
+    return json.load(open(os.path.join(bench.ROOT, "tests", "golden", name + ".json")))
+
+
+def test_nb_alpha_on_hand_worked_batches():
+    """Batched transfers (Sec. V): batches holding some token's first step
+    (one parallel extraction) plus batches holding some token's last step
+    (one parallel implantation)."""
+    # equal_exchange: batch 0 moves both tokens off their traps (one
+    # extraction batch); move 0 ends in batch 1, move 1 in batch 2
+    fx = _fixture("equal_exchange")
+    assert bench.nb_alpha(fx["ops"], fx["members"]) == 1 + 2
+    # many_to_one_redrec: both start in batch 0; move 0 ends in batch 1,
+    # move 1 in batch 4
+    fx = _fixture("many_to_one_redrec")
+    assert bench.nb_alpha(fx["ops"], fx["members"]) == 1 + 2
+    # the 2n chain: every batch holds one token, so no transfer is shared:
+    # NB_alpha = N_alpha = 2 per move
+    fx = _fixture("chain_2n")
+    assert bench.nb_alpha(fx["ops"], fx["members"]) == 2 * len(fx["moves"])
+    assert bench.nb_alpha(np.zeros((0, 3), np.int32), np.zeros(0, np.int32)) == 0
+
+
+def test_served_requests_are_distinct_grids():
+    a = [bench.served_grid(5, i) for i in range(6)]
+    assert all(s in gridgen.SIDES_SERVED for _, _, s in a)
+    assert len({(w.tobytes(), s) for w, _, s in a}) == 6
+    w, rect, s = bench.served_grid(5, 3)
+    assert rect == gridgen.centred_rect(s, s, int(0.7 * s), int(0.7 * s))
+    assert (w == bench.served_grid(5, 3)[0]).all()
 
 
 def test_paper_instances_are_the_paper_geometry_and_feasible():
