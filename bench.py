@@ -775,7 +775,6 @@ def run_ours(args, rank, world, local):
     grid_bytes = host.numel() * 4
     alg = {
         "k_sim": 16 * tot_moves + 12 * tot_ops + 4 * tot_mem,
-        "k_bsort": 8 * (tot_mem + tot_moves),
         "k_emit_recv": 16 * tot_moves,
         "k_transpose": 2 * grid_bytes,
     }

@@ -294,6 +294,15 @@ int rr_plan_noalloc(const void *d_grid, int layout, int m, int n, rr_rect rect,
 int rr_set_tracing(rr_ctx *ctx, int enable);
 int rr_stage_times(rr_ctx *ctx, float *ms, const char **names, int cap);
 
+/* Test hook for the failure path (nothing in the paper corresponds to it):
+ * with limit > 0 the pairing loop of the planner (Alg. 1) and the batching
+ * simulation (Alg. 4) stop after `limit` iterations and report
+ * RR_ERR_TIMEOUT, exactly as when their built-in iteration bounds run out, so
+ * that a test can drive that path without a fault; limit 0 restores the
+ * built-in bounds. It holds for every context of the process on the current
+ * device; not for production use. Returns RR_ERR_ARG for a negative limit. */
+int rr_debug_guard_limit(int64_t limit);
+
 /* Kernels this context has launched since it was created (every public call
  * adds the launches it made; the size-class simulation counts one launch per
  * class). For accounting only: reading it does not synchronise. Returns

@@ -67,7 +67,7 @@ class rr_serve_result(ctypes.Structure):
 
 
 EXPORTS = ("rr_ctx_create", "rr_ctx_destroy", "rr_plan", "rr_bird_plan", "rr_plan_mode", "rr_batch", "rr_plan_batched", "rr_set_tracing",
-           "rr_stage_times", "rr_launch_count", "rr_autotune", "rr_set_config", "rr_last_error", "rr_plan_noalloc", "rr_plan_one", "rr_serve_open", "rr_serve_submit",
+           "rr_stage_times", "rr_launch_count", "rr_autotune", "rr_set_config", "rr_last_error", "rr_plan_noalloc", "rr_plan_one", "rr_debug_guard_limit", "rr_serve_open", "rr_serve_submit",
            "rr_serve_poll", "rr_serve_release", "rr_serve_close")
 RR_NOALLOC_MAX_SIDE = 256
 RR_ONE_MAX_SIDE = 256
@@ -113,6 +113,8 @@ def load(path: str = LIB_PATH):
     L.rr_plan_noalloc.restype = I32
     L.rr_plan_one.argtypes = [P, P, I32, I32, I32, rr_rect, I32, P, I64, P, I64, P, I64, ctypes.POINTER(I64), P]
     L.rr_plan_one.restype = I32
+    L.rr_debug_guard_limit.argtypes = [I64]
+    L.rr_debug_guard_limit.restype = I32
     L.rr_serve_open.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(rr_serve_config)]
     L.rr_serve_open.restype = I32
     L.rr_serve_submit.argtypes = [P, P, I32, I32, I32, rr_rect, ctypes.POINTER(I64)]
@@ -269,6 +271,12 @@ def rr_plan_one(ctx, d_grid, layout, m, n, rect, flags, d_moves, cap_moves, d_op
                             int(flags), _addr(d_moves), int(cap_moves), _addr(d_ops), int(cap_ops), _addr(d_members),
                             int(cap_members), counts, _stream(stream))
     return (st, *[int(c) for c in counts])
+
+
+def rr_debug_guard_limit(limit: int) -> int:
+    """Caps the pairing loop and the batching simulation at `limit`
+    iterations (0: the built-in bounds), for tests of the timeout path."""
+    return load().rr_debug_guard_limit(int(limit))
 
 
 # ------------------------------------------------------------------ serving

@@ -5,9 +5,14 @@
 
 namespace rrk {
 
-__global__ void k_bsetup(rr_instance *inst, JobWS *wsv, int count, Arena A)
+__global__ void k_bsetup(rr_instance *inst, JobWS *wsv, int count, Arena A, int lookback)
 {
-    s_bsetup(hw_blk(), inst, wsv, count, A);
+    s_bsetup(hw_blk(), inst, wsv, count, A, lookback);
+}
+
+__global__ void __launch_bounds__(LB_THREADS) k_pairoff_lookback(rr_instance *inst, JobWS *wsv, int count, Arena A)
+{
+    s_pairoff_lookback(hw_blk(), inst, wsv, count, A);
 }
 
 __global__ void k_gcount(rr_instance *inst, JobWS *wsv, int count)
@@ -38,31 +43,6 @@ __global__ void k_gsweep_h(rr_instance *inst, JobWS *wsv, int count, int lineCap
 __global__ void k_gsweep_v(rr_instance *inst, JobWS *wsv, int count, int lineCap)
 {
     s_gsweep_v(hw_blk(), inst, wsv, count, lineCap);
-}
-
-__global__ void k_galloc(rr_instance *inst, JobWS *wsv, int count, Arena A)
-{
-    s_galloc(hw_blk(), inst, wsv, count, A);
-}
-
-__global__ void k_bcount(rr_instance *inst, JobWS *wsv, int count)
-{
-    s_bcount(hw_blk(), inst, wsv, count);
-}
-
-__global__ void k_bscan_cells(rr_instance *inst, JobWS *wsv, int count)
-{
-    s_bscan_cells(hw_blk(), inst, wsv, count);
-}
-
-__global__ void k_bfill(rr_instance *inst, JobWS *wsv, int count)
-{
-    s_bfill(hw_blk(), inst, wsv, count);
-}
-
-__global__ void k_bsort(rr_instance *inst, JobWS *wsv, int count)
-{
-    s_bsort(hw_blk(), inst, wsv, count);
 }
 
 __global__ void k_bsucc(rr_instance *inst, JobWS *wsv, int count)
@@ -121,6 +101,11 @@ __global__ void k_sim32w(rr_instance *inst, JobWS *wsv, int count, const int *cl
                          int slotCap, int lineCap)
 {
     sim_body<int32_t, true>(hw_blk(), inst, wsv, count, classList, classCount, slotCap, lineCap);
+}
+
+int guard_cap_batch(long long cap)
+{
+    return cudaMemcpyToSymbol(g_guard_cap, &cap, sizeof(cap)) == cudaSuccess ? RR_OK : RR_ERR_CUDA;
 }
 
 } // namespace rrk

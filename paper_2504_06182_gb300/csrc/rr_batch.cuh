@@ -62,20 +62,9 @@ __device__ inline long long block_exclusive_scan(int32_t *v, int len, long long 
     return total;
 }
 
-// Position of vertex (r, c) along move p (row first, then column).
-__device__ __forceinline__ int path_pos(const rr_move &p, int r, int c)
-{
-    const int hl = iabs(p.dst_col - p.src_col);
-    if (r == p.src_row) {
-        const int t = iabs(c - p.src_col);
-        if (t <= hl && ((c - p.src_col) * (p.dst_col - p.src_col) >= 0)) return t;
-    }
-    return hl + iabs(r - p.src_row);
-}
-
 // ----------------------------------------------------------- set-up pass
 // One block per instance: check the moves, count path vertices, allocate.
-__device__ inline void s_bsetup(const Blk B, rr_instance *inst, JobWS *wsv, int count, Arena A)
+__device__ inline void s_bsetup(const Blk B, rr_instance *inst, JobWS *wsv, int count, Arena A, int lookback)
 {
     __shared__ long long s_tmp[34];
     __shared__ int s_bad;
@@ -86,6 +75,47 @@ __device__ inline void s_bsetup(const Blk B, rr_instance *inst, JobWS *wsv, int 
     JobWS &ws = wsv[q];
     const int m = I->m, n = I->n;
     const int64_t k = I->n_moves;
+    if (lookback && k >= LB_MIN_MOVES) {
+        // a large move list: checking the moves, counting their vertices and
+        // the offsets are the work of the multi-block k_pairoff_lookback,
+        // which also allocates the vertex-sized arrays once the total is
+        // known; here only the move-sized arrays
+        __shared__ int s_ok;
+        if (threadIdx.x == 0) {
+            bool ok = k <= 0x3fffffff;
+            const unsigned long long cells = (unsigned long long)m * n;
+            if (!ok) I->status = RR_ERR_ARG;
+            ws.P = -1;
+            ws.pairOff = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
+            ws.colOff = (int32_t *)arena_alloc(A, 4ull * (n + 1), &ok);
+            ws.colCur = (int32_t *)arena_alloc(A, 4ull * (n + 1), &ok);
+            ws.colList = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
+            ws.rowOff = (int32_t *)arena_alloc(A, 4ull * (m + 1), &ok);
+            ws.rowCur = (int32_t *)arena_alloc(A, 4ull * (m + 1), &ok);
+            ws.rowList = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
+            ws.firstH = (int32_t *)arena_alloc(A, 4ull * cells, &ok);
+            ws.succCnt = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
+            ws.indeg = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
+            ws.rec = (int4 *)arena_alloc(A, 32ull * (k + 1), &ok);
+            ws.succ4 = ws.rec + 1;
+            ws.ready0 = (int32_t *)arena_alloc(A, 4ull * (k + 1) + 16, &ok);
+            ws.slotOvf = arena_alloc(A, 40ull * (k + 1), &ok);
+            ws.ovfFree = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
+            ws.nextAt = nullptr;
+            ws.succ = nullptr;
+            ws.lbStatus = (unsigned long long *)arena_alloc(A, 8ull * ((k + LB_TILE - 1) / LB_TILE), &ok);
+            ws.lbCounter = (int32_t *)arena_alloc(A, 4, &ok);
+            if (!ok && live(I)) I->status = RR_ERR_WORKSPACE;
+            s_ok = live(I);
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        for (int64_t t = threadIdx.x; t < (k + LB_TILE - 1) / LB_TILE; t += blockDim.x) ws.lbStatus[t] = 0ull;
+        if (threadIdx.x == 0) { *ws.lbCounter = 0; ws.ready0[k] = 0; }
+        for (int c = threadIdx.x; c <= n; c += blockDim.x) { ws.colOff[c] = 0; ws.colCur[c] = 0; }
+        for (int r = threadIdx.x; r <= m; r += blockDim.x) { ws.rowOff[r] = 0; ws.rowCur[r] = 0; }
+        return;
+    }
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
     long long P = 0, steps = 0;
@@ -118,8 +148,6 @@ __device__ inline void s_bsetup(const Blk B, rr_instance *inst, JobWS *wsv, int 
             const unsigned long long cells = (unsigned long long)m * n;
             ws.P = tp;
             ws.pairOff = (int32_t *)arena_alloc(A, 4ull * (k + 1), &ok);
-            ws.cellCnt = nullptr; ws.cellCur = nullptr; ws.cover = nullptr;   // only if the sweeps do not apply
-            ws.genericGamma = 0;
             ws.nextAt = (int32_t *)arena_alloc(A, 4ull * (tp + 1), &ok);
             ws.colOff = (int32_t *)arena_alloc(A, 4ull * (n + 1), &ok);
             ws.colCur = (int32_t *)arena_alloc(A, 4ull * (n + 1), &ok);
@@ -138,6 +166,8 @@ __device__ inline void s_bsetup(const Blk B, rr_instance *inst, JobWS *wsv, int 
             // a path has at most as many distinct successors as vertices: they
             // are stored at the path's vertex offset, so no count pass or scan
             ws.succ = (int32_t *)arena_alloc(A, 4ull * (tp + 1), &ok);
+            ws.lbStatus = nullptr;
+            ws.lbCounter = nullptr;
             if (!ok) I->status = RR_ERR_WORKSPACE;
         }
     }
@@ -157,6 +187,153 @@ __device__ inline void s_bsetup(const Blk B, rr_instance *inst, JobWS *wsv, int 
     if (threadIdx.x == 0) ws.pairOff[k] = (int32_t)tot;
 }
 
+// Path-vertex offsets of a large move list: pairOff[b] = sum over a < b of
+// (path length + 1), by a single pass of decoupled look-back (Merrill and
+// Garland, "Single-pass parallel prefix scan with decoupled look-back",
+// 2016). Blocks take tiles of LB_TILE moves in order from the instance's
+// counter (so every tile a block waits on is held by a running block); a
+// tile publishes its aggregate at once and, once its exclusive prefix is
+// known from the preceding tiles' words, its inclusive prefix. Status word:
+// flag in the top two bits (0 not ready, 1 aggregate, 2 inclusive prefix),
+// value in the low 62. Waits are bounded: a block that sees no progress for
+// LB_SPIN_LIMIT polls sets RR_ERR_TIMEOUT and stops. The same pass checks
+// every move, clears the in-degrees, and the block of the last tile, which
+// learns the total, counts the elementary steps, checks the output room and
+// allocates the vertex-sized arrays.
+constexpr unsigned long long LB_AGG = 1ull << 62, LB_INCL = 2ull << 62, LB_VAL = (1ull << 62) - 1;
+constexpr int LB_SPIN_LIMIT = 1 << 22;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ inline void s_pairoff_lookback(const Blk B, rr_instance *inst, JobWS *wsv, int count, Arena A)
+{
+    __shared__ long long s_warp[LB_THREADS / 32];
+    __shared__ long long s_excl;
+    __shared__ int s_tile, s_stop;
+    const int q = B.y;
+    if (q >= count) return;
+    rr_instance *I = &inst[q];
+    if (!live(I)) return;
+    JobWS &ws = wsv[q];
+    if (!ws.lbStatus) return;
+    const int64_t k = I->n_moves;
+    const int ntile = (int)((k + LB_TILE - 1) / LB_TILE);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (;;) {
+        if (tid == 0) { s_tile = atomicAdd(ws.lbCounter, 1); s_stop = 0; }
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= ntile) break;
+        // this thread's LB_ITEMS consecutive moves
+        const int64_t b0 = (int64_t)tile * LB_TILE + (int64_t)tid * LB_ITEMS;
+        int v[LB_ITEMS];
+        long long sum = 0;
+        bool bad = false;
+        const int m = I->m, n = I->n;
+#pragma unroll
+        for (int u = 0; u < LB_ITEMS; ++u) {
+            const int64_t b = b0 + u;
+            v[u] = 0;
+            if (b < k) {
+                const rr_move p = I->moves[b];
+                bad |= p.src_row < 0 || p.src_row >= m || p.dst_row < 0 || p.dst_row >= m || p.src_col < 0 ||
+                       p.src_col >= n || p.dst_col < 0 || p.dst_col >= n ||
+                       (p.src_row == p.dst_row && p.src_col == p.dst_col);
+                v[u] = iabs(p.dst_col - p.src_col) + iabs(p.dst_row - p.src_row) + 1;
+                ws.indeg[b] = 0;
+            }
+            sum += v[u];
+        }
+        if (bad) set_status(I, RR_ERR_ARG);
+        // block scan of the thread sums
+        long long incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const long long w = lane < LB_THREADS / 32 ? s_warp[lane] : 0;
+            long long wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long t = __shfl_up_sync(FULL, wi, o);
+                if (lane >= o) wi += t;
+            }
+            if (lane < LB_THREADS / 32) s_warp[lane] = wi - w;
+            const long long agg = __shfl_sync(FULL, wi, 31);
+            if (lane == 0) {
+                unsigned long long *st = ws.lbStatus;
+                long long excl = 0;
+                if (tile == 0) {
+                    st_release_u64(&st[0], LB_INCL | (unsigned long long)agg);
+                } else {
+                    st_release_u64(&st[tile], LB_AGG | (unsigned long long)agg);
+                    int j = tile - 1, spins = 0;
+                    while (j >= 0) {
+                        const unsigned long long w2 = ld_acquire_u64(&st[j]);
+                        const unsigned long long f = w2 & ~LB_VAL;
+                        if (f == 0ull) {
+                            if (++spins > LB_SPIN_LIMIT) { s_stop = 1; break; }
+                            __nanosleep(32);
+                            continue;
+                        }
+                        spins = 0;
+                        excl += (long long)(w2 & LB_VAL);
+                        if (f == LB_INCL) break;
+                        --j;
+                    }
+                    if (!s_stop) st_release_u64(&st[tile], LB_INCL | (unsigned long long)(excl + agg));
+                }
+                s_excl = excl;
+                if (tile == ntile - 1 && !s_stop) {
+                    // the total: elementary steps, the room they need, and
+                    // the vertex-sized arrays (as the one-block set-up does)
+                    const long long tp = excl + agg, ts = tp - k;
+                    I->n_steps = ts;
+                    I->n_members = ts;
+                    if (tp > 0x7fffffffLL) {
+                        set_status(I, RR_ERR_ARG);
+                    } else if (ts > I->cap_members || (ts > 0 && (!I->members || !I->ops))) {
+                        if (atomicCAS(&I->status, RR_OK, RR_ERR_CAPACITY) == RR_OK) I->n_ops = ts;
+                    } else {
+                        bool ok = true;
+                        ws.P = tp;
+                        ws.pairOff[k] = (int32_t)tp;
+                        ws.nextAt = (int32_t *)arena_alloc(A, 4ull * (tp + 1), &ok);
+                        ws.succ = (int32_t *)arena_alloc(A, 4ull * (tp + 1), &ok);
+                        if (!ok) set_status(I, RR_ERR_WORKSPACE);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (s_stop) {
+            if (tid == 0) set_status(I, RR_ERR_TIMEOUT);
+            break;
+        }
+        long long run = s_excl + s_warp[wid] + incl - sum;
+#pragma unroll
+        for (int u = 0; u < LB_ITEMS; ++u) {
+            const int64_t b = b0 + u;
+            if (b < k) ws.pairOff[b] = (int32_t)run;
+            run += v[u];
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- Gamma
 // Vertex (r, c) is covered by the vertical parts of the moves ending in
 // column c (the corner of an L-move included) and by the horizontal parts of
@@ -167,8 +344,8 @@ __device__ inline void s_bsetup(const Blk B, rr_instance *inst, JobWS *wsv, int 
 // coverer precedes every horizontal one (a corridor only crosses a column
 // after that column's moves were emitted), so the chains are concatenated;
 // elsewhere (bird's corridors cross columns solved later) the column sweep
-// merges the two chains of that vertex by id. Per-vertex path lists remain
-// as the fallback for a chain too long to merge.
+// merges the two chains of that vertex by id (a chain holds each move at
+// most once, so a merge takes at most k steps; more is an invariant failure).
 
 __device__ inline void s_gcount(const Blk B, rr_instance *inst, JobWS *wsv, int count)
 {
@@ -325,9 +502,6 @@ __device__ inline void s_gsweep_h(const Blk B, rr_instance *inst, JobWS *wsv, in
     }
 }
 
-// Longest coverer chain one lane merges at a vertex; an instance with a longer
-// one takes the per-vertex fallback.
-constexpr int MERGE_LIMIT = 1 << 16;
 
 // Column sweep: the moves ending in each column in id order; consecutive
 // vertical coverers are linked, the last one to the vertex's first
@@ -339,11 +513,12 @@ __device__ inline void s_gsweep_v(const Blk B, rr_instance *inst, JobWS *wsv, in
     extern __shared__ int32_t sweepbuf[];
     const int q = B.y;
     if (q >= count) return;
-    const rr_instance *I = &inst[q];
+    rr_instance *I = &inst[q];
     if (!live(I)) return;
     JobWS &ws = wsv[q];
     const int lane = threadIdx.x & 31;
     const int n = I->n, m = I->m;
+    const int64_t k = I->n_moves;
     int32_t *lastPos = sweepbuf + (threadIdx.x >> 5) * 3 * lineCap;
     int32_t *lastId = lastPos + lineCap;
     int32_t *firstId = lastId + lineCap;
@@ -376,8 +551,9 @@ __device__ inline void s_gsweep_v(const Blk B, rr_instance *inst, JobWS *wsv, in
             }
             // merge: take the smaller id of the two chain heads, link it
             // after the previous one, advance its chain
-            int v = firstId[r], h = f, prevEntry = -1, steps = 0;
-            for (; (v >= 0 || h >= 0) && steps < MERGE_LIMIT; ++steps) {
+            int v = firstId[r], h = f, prevEntry = -1;
+            int64_t steps = 0;
+            for (; (v >= 0 || h >= 0) && steps <= k; ++steps) {   // a chain holds each move at most once
                 const bool takeV = h < 0 || (v >= 0 && v < h);
                 const int x = takeV ? v : h;
                 const rr_move p = I->moves[x];
@@ -389,124 +565,10 @@ __device__ inline void s_gsweep_v(const Blk B, rr_instance *inst, JobWS *wsv, in
                 if (takeV) v = nx; else h = nx;
             }
             if (prevEntry >= 0) ws.nextAt[prevEntry] = -1;
-            bad |= steps >= MERGE_LIMIT;
+            bad |= steps > k;
         }
-        if (__any_sync(FULL, bad) && lane == 0) ws.genericGamma = 1;
+        if (__any_sync(FULL, bad) && lane == 0) set_status(I, RR_ERR_INTERNAL);
         __syncwarp();
-    }
-}
-
-// Per-vertex lists for the instances the sweeps cannot serve.
-__device__ inline void s_galloc(const Blk B, rr_instance *inst, JobWS *wsv, int count, Arena A)
-{
-    const int q = B.x;
-    if (q >= count) return;
-    rr_instance *I = &inst[q];
-    if (!live(I)) return;
-    JobWS &ws = wsv[q];
-    if (!ws.genericGamma) return;
-    __shared__ int s_ok;
-    const unsigned long long cells = (unsigned long long)I->m * I->n;
-    if (threadIdx.x == 0) {
-        bool ok = true;
-        ws.cellCnt = (int32_t *)arena_alloc(A, 4ull * (cells + 1), &ok);
-        ws.cellCur = (int32_t *)arena_alloc(A, 4ull * cells, &ok);
-        ws.cover = (int32_t *)arena_alloc(A, 4ull * (ws.P + 1), &ok);
-        s_ok = ok;
-        if (!ok) I->status = RR_ERR_WORKSPACE;
-    }
-    __syncthreads();
-    if (!s_ok) return;
-    for (unsigned long long v = threadIdx.x; v < cells; v += blockDim.x) { ws.cellCnt[v] = 0; ws.cellCur[v] = 0; }
-}
-
-// Vertex counts per cell.
-__device__ inline void s_bcount(const Blk B, rr_instance *inst, JobWS *wsv, int count)
-{
-    const int q = B.y;
-    if (q >= count) return;
-    const rr_instance *I = &inst[q];
-    if (!live(I)) return;
-    JobWS &ws = wsv[q];
-    if (!ws.genericGamma) return;
-    const int n = I->n;
-    const int64_t k = I->n_moves;
-    for (int64_t b = B.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)B.gx * blockDim.x) {
-        const rr_move p = I->moves[b];
-        const int len = iabs(p.dst_col - p.src_col) + iabs(p.dst_row - p.src_row);
-        for (int t = 0; t <= len; ++t) {
-            int r, c; path_cell(p.src_row, p.src_col, p.dst_row, p.dst_col, t, &r, &c);
-            atomicAdd(&ws.cellCnt[(size_t)r * n + c], 1);
-        }
-    }
-}
-
-__device__ inline void s_bscan_cells(const Blk B, rr_instance *inst, JobWS *wsv, int count)
-{
-    __shared__ long long s_tmp[34];
-    const int q = B.x;
-    if (q >= count) return;
-    rr_instance *I = &inst[q];
-    if (!live(I)) return;
-    JobWS &ws = wsv[q];
-    if (!ws.genericGamma) return;
-    const int cells = I->m * I->n;
-    const long long tot = block_exclusive_scan(ws.cellCnt, cells, s_tmp);
-    if (threadIdx.x == 0) {
-        ws.cellCnt[cells] = (int32_t)tot;
-        if (tot != ws.P) I->status = RR_ERR_INTERNAL;
-    }
-}
-
-__device__ inline void s_bfill(const Blk B, rr_instance *inst, JobWS *wsv, int count)
-{
-    const int q = B.y;
-    if (q >= count) return;
-    const rr_instance *I = &inst[q];
-    if (!live(I)) return;
-    JobWS &ws = wsv[q];
-    if (!ws.genericGamma) return;
-    const int n = I->n;
-    const int64_t k = I->n_moves;
-    for (int64_t b = B.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)B.gx * blockDim.x) {
-        const rr_move p = I->moves[b];
-        const int len = iabs(p.dst_col - p.src_col) + iabs(p.dst_row - p.src_row);
-        for (int t = 0; t <= len; ++t) {
-            int r, c; path_cell(p.src_row, p.src_col, p.dst_row, p.dst_col, t, &r, &c);
-            const size_t v = (size_t)r * n + c;
-            ws.cover[ws.cellCnt[v] + atomicAdd(&ws.cellCur[v], 1)] = (int32_t)b;
-        }
-    }
-}
-
-// Per cell: order its paths by id, then record for each path the next path
-// through this cell (or -1) at the path's own vertex index.
-__device__ inline void s_bsort(const Blk B, rr_instance *inst, JobWS *wsv, int count)
-{
-    const int q = B.y;
-    if (q >= count) return;
-    const rr_instance *I = &inst[q];
-    if (!live(I)) return;
-    JobWS &ws = wsv[q];
-    if (!ws.genericGamma) return;
-    const int n = I->n;
-    const long long cells = (long long)I->m * n;
-    for (long long v = B.x * blockDim.x + threadIdx.x; v < cells; v += (long long)B.gx * blockDim.x) {
-        const int lo = ws.cellCnt[v], hi = ws.cellCnt[v + 1];
-        if (hi == lo) continue;
-        int32_t *L = ws.cover + lo;
-        for (int i = 1; i < hi - lo; ++i) {
-            const int32_t x = L[i];
-            int j = i - 1;
-            while (j >= 0 && L[j] > x) { L[j + 1] = L[j]; --j; }
-            L[j + 1] = x;
-        }
-        const int r = (int)(v / n), c = (int)(v % n);
-        for (int i = 0; i < hi - lo; ++i) {
-            const int32_t a = L[i];
-            const rr_move p = I->moves[a];
-            ws.nextAt[ws.pairOff[a] + path_pos(p, r, c)] = (i + 1 < hi - lo) ? L[i + 1] : -1;
-        }
     }
 }
 
@@ -1108,7 +1170,7 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
     // index lineIdx, direction dm
     int nm = 0, dm = -1, lineIdx = -1;
     bool rowLine = true;
-    const int64_t guard_max = I->n_steps + 2ll * k + 16;
+    const int64_t guard_max = g_guard_cap > 0 ? g_guard_cap : I->n_steps + 2ll * k + 16;
     int64_t guard = 0;
 
     while (!err && L < k) {

@@ -15,18 +15,14 @@ __global__ void k_pair(rr_instance *, JobWS *, int);
 __global__ void k_emit_cols(rr_instance *, JobWS *, int);
 __global__ void k_emit_recv(rr_instance *, JobWS *, int);
 __global__ void k_bird(rr_instance *, JobWS *, int, int);
-__global__ void k_bsetup(rr_instance *, JobWS *, int, Arena);
+__global__ void k_bsetup(rr_instance *, JobWS *, int, Arena, int);
+__global__ void k_pairoff_lookback(rr_instance *, JobWS *, int, Arena);
 __global__ void k_gcount(rr_instance *, JobWS *, int);
 __global__ void k_gscan(rr_instance *, JobWS *, int);
 __global__ void k_gfill(rr_instance *, JobWS *, int);
 __global__ void k_gsort(rr_instance *, JobWS *, int, int);
 __global__ void k_gsweep_h(rr_instance *, JobWS *, int, int);
 __global__ void k_gsweep_v(rr_instance *, JobWS *, int, int);
-__global__ void k_galloc(rr_instance *, JobWS *, int, Arena);
-__global__ void k_bcount(rr_instance *, JobWS *, int);
-__global__ void k_bscan_cells(rr_instance *, JobWS *, int);
-__global__ void k_bfill(rr_instance *, JobWS *, int);
-__global__ void k_bsort(rr_instance *, JobWS *, int);
 __global__ void k_bsucc(rr_instance *, JobWS *, int);
 __global__ void k_brec(rr_instance *, JobWS *, int);
 __global__ void k_classify(rr_instance *, int, int, int, int *, int *);
@@ -51,6 +47,7 @@ enum { SM_GSORT, SM_GSWEEP_H, SM_GSWEEP_V, SM_SIM16, SM_SIM32, SM_SIM16W, SM_SIM
 
 struct rr_ctx {
     int device;
+    int nsm;                     // streaming multiprocessors of the device
     int smemLimit[SM_NKERNEL];   // dynamic shared memory each of those kernels may request
     char *arena;
     unsigned long long arena_size;
@@ -200,6 +197,7 @@ extern "C" int rr_ctx_create(rr_ctx **out, int64_t arena_bytes)
     ctx->pipe = 1;
     if (arena_bytes <= 0) arena_bytes = 1ll << 30;
     cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->arena, (size_t)arena_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_top, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_one, sizeof(rr_instance));
@@ -369,9 +367,17 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, 
 {
     const Arena A = arena_of(ctx);
     const int pathBlocks = clampi(std::max(1, budget(ctx, 8192) / count), 1, 512);
-    const int cellBlocks = clampi(std::max(1, budget(ctx, 8192) / count), 1, (max_side * max_side + 255) / 256);
+    // move lists long enough for it (grids above 256 on a side) get their
+    // path-vertex offsets from the multi-block look-back scan
+    const int lookback = max_side > 256 ? 1 : 0;
     mark(ctx, s, "k_bsetup");
-    k_bsetup<<<count, 512, 0, s>>>(d_inst, ws, count, A);
+    k_bsetup<<<count, 512, 0, s>>>(d_inst, ws, count, A, lookback);
+    if (lookback) {
+        mark(ctx, s, "k_pairoff_lookback");
+        k_pairoff_lookback<<<dim3(clampi(2 * ctx->nsm / count, 1, 2 * ctx->nsm), count), LB_THREADS, 0, s>>>(
+            d_inst, ws, count, A);
+        ctx->nlaunch += 1;
+    }
     {
         // Gamma by column and row sweeps (per-vertex lists only where they fail)
         const int lineBlocks = clampi(std::max(1, budget(ctx, 8192) / count), 1, (2 * max_side + 7) / 8);
@@ -392,17 +398,7 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, 
         k_gsweep_h<<<dim3(lineBlocks, count), 256, 8 * 4 * (size_t)max_side, s>>>(d_inst, ws, count, max_side);
         mark(ctx, s, "k_gsweep_v");
         k_gsweep_v<<<dim3(lineBlocks, count), 256, 8 * 12 * (size_t)max_side, s>>>(d_inst, ws, count, max_side);
-        mark(ctx, s, "k_galloc");
-        k_galloc<<<count, 256, 0, s>>>(d_inst, ws, count, A);
     }
-    mark(ctx, s, "k_bcount");
-    k_bcount<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ws, count);
-    mark(ctx, s, "k_bscan_cells");
-    k_bscan_cells<<<count, 1024, 0, s>>>(d_inst, ws, count);
-    mark(ctx, s, "k_bfill");
-    k_bfill<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ws, count);
-    mark(ctx, s, "k_bsort");
-    k_bsort<<<dim3(cellBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_bsucc");
     k_bsucc<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ws, count);
     mark(ctx, s, "k_brec");
@@ -459,7 +455,7 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, 
     }
     mark(ctx, s, nullptr);
     CUDA_TRY(cudaGetLastError());
-    ctx->nlaunch += (one ? 14 : 15) + 2 * nclass;
+    ctx->nlaunch += (one ? 9 : 10) + 2 * nclass;
     return RR_OK;
 }
 
@@ -785,6 +781,15 @@ extern "C" int rr_set_config(rr_ctx *ctx, int nclass, int shift, int pipe)
 // Library-internal: size a context's descriptor table for `count` instances
 // up front (the server does this before any wave so that no call allocates).
 int rr_internal_reserve(rr_ctx *ctx, int count) { return ensure_ws(ctx, count); }
+
+extern "C" int rr_debug_guard_limit(int64_t limit)
+{
+    if (limit < 0) return fail(nullptr, RR_ERR_ARG, "rr_debug_guard_limit: negative limit");
+    int st = guard_cap_plan(limit);
+    if (st == RR_OK) st = guard_cap_batch(limit);
+    if (st == RR_OK) st = guard_cap_one(limit);
+    return st == RR_OK ? RR_OK : fail(nullptr, st, "rr_debug_guard_limit: %s", cudaGetErrorString(cudaGetLastError()));
+}
 
 extern "C" int rr_set_tracing(rr_ctx *ctx, int enable)
 {

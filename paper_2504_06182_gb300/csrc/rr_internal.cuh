@@ -76,9 +76,6 @@ struct JobWS {
     // batching (Gamma + simulation)
     int64_t P;             // total path vertices (sum of path length + 1)
     int32_t *pairOff;      // k + 1
-    int32_t *cellCnt;      // m * n + 1 (counts, then exclusive offsets)
-    int32_t *cellCur;      // m * n
-    int32_t *cover;        // P
     int32_t *nextAt;       // P
     int32_t *succCnt;      // k: distinct successors of each path
     int32_t *succ;         // P: a path's successors at its vertex offset (pairOff)
@@ -90,10 +87,20 @@ struct JobWS {
     int32_t *colOff, *colCur, *colList;   // n + 1, n, k
     int32_t *rowOff, *rowCur, *rowList;   // m + 1, m, k
     int32_t *firstH;       // m * n: lowest-id L-move crossing each vertex, -1
-    int32_t genericGamma;  // set when the sweep order does not hold: per-vertex lists instead
     void *slotOvf;         // k simulation slots beyond the shared-memory ones
     int32_t *ovfFree;      // k: recycled overflow slots
+    // path-vertex offsets by the multi-block scan (large move lists only):
+    // one status word per tile, the tile counter
+    unsigned long long *lbStatus;
+    int32_t *lbCounter;
 };
+
+// Multi-block single-pass scan (decoupled look-back) of the path-vertex
+// offsets: tiles of LB_TILE moves, taken in order from a per-instance
+// counter by blocks of LB_THREADS threads; used for move lists of at least
+// LB_MIN_MOVES (below that one block scans them).
+constexpr int LB_THREADS = 512, LB_ITEMS = 8, LB_TILE = LB_THREADS * LB_ITEMS;
+constexpr int64_t LB_MIN_MOVES = 1 << 16;
 
 // Side bound of simulation size class c of nclass over grids up to
 // max_side (the last class takes max_side itself).
@@ -195,6 +202,12 @@ __device__ __forceinline__ void path_cell(int sr, int sc, int dr, int dc, int t,
     else { *r = sr + (t - hl) * isgn(dr - sr); *c = dc; }
 }
 
+// Test hook: when positive, the pairing loop and the batching simulation
+// stop after this many iterations with RR_ERR_TIMEOUT, as when their own
+// bounds run out (rr_debug_guard_limit sets it in every module that runs
+// them). Zero keeps the built-in bounds.
+static __device__ long long g_guard_cap = 0;
+
 // Status helpers: an instance is live while its status is RR_OK.
 __device__ __forceinline__ void set_status(rr_instance *I, int st)
 {
@@ -252,6 +265,10 @@ __device__ __forceinline__ int band_P(const int16_t *hr, int nh, int nband, int 
 int rr_internal_reserve(rr_ctx *ctx, int count);
 
 namespace rrk {
+// Per-module setters of g_guard_cap (rr_plan.cu, rr_batch.cu, rr_one.cu).
+int guard_cap_plan(long long cap);
+int guard_cap_batch(long long cap);
+int guard_cap_one(long long cap);
 // The single-grid kernel (rr_one.cu): one block of ONE_THREADS threads runs
 // planning, Gamma and batching of one grid with sides up to ONE_MAX_SIDE.
 constexpr int ONE_THREADS = 256;

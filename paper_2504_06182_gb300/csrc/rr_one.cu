@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(ONE_THREADS) k_one(rr_instance h, rr_instance 
     }
     __syncthreads();
     if (batch && I->status == RR_OK) {          // read after a barrier: the same in every thread
-        s_bsetup(B, I, ws, 1, A);
+        s_bsetup(B, I, ws, 1, A, 0);
         __syncthreads();
         s_gcount(B, I, ws, 1);
         __syncthreads();
@@ -63,16 +63,6 @@ __global__ void __launch_bounds__(ONE_THREADS) k_one(rr_instance h, rr_instance 
         s_gsweep_h(B, I, ws, 1, side);
         __syncthreads();
         s_gsweep_v(B, I, ws, 1, side);
-        __syncthreads();
-        s_galloc(B, I, ws, 1, A);
-        __syncthreads();
-        s_bcount(B, I, ws, 1);
-        __syncthreads();
-        s_bscan_cells(B, I, ws, 1);
-        __syncthreads();
-        s_bfill(B, I, ws, 1);
-        __syncthreads();
-        s_bsort(B, I, ws, 1);
         __syncthreads();
         s_bsucc(B, I, ws, 1);
         __syncthreads();
@@ -118,6 +108,11 @@ int one_launch(rr_instance h, rr_instance *d_inst, JobWS *d_ws, Arena A, int fla
     while (P2 < side) P2 <<= 1;
     k_one<<<1, ONE_THREADS, smem, s>>>(h, d_inst, d_ws, A, flags, side, P2, hostOut);
     return cudaGetLastError() == cudaSuccess ? RR_OK : RR_ERR_CUDA;
+}
+
+int guard_cap_one(long long cap)
+{
+    return cudaMemcpyToSymbol(g_guard_cap, &cap, sizeof(cap)) == cudaSuccess ? RR_OK : RR_ERR_CUDA;
 }
 
 } // namespace rrk

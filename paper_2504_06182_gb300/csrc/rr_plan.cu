@@ -35,4 +35,9 @@ __global__ void k_emit_recv(rr_instance *inst, JobWS *wsv, int count)
     s_emit_recv(hw_blk(), inst, wsv, count);
 }
 
+int guard_cap_plan(long long cap)
+{
+    return cudaMemcpyToSymbol(g_guard_cap, &cap, sizeof(cap)) == cudaSuccess ? RR_OK : RR_ERR_CUDA;
+}
+
 } // namespace rrk

@@ -286,7 +286,7 @@ __device__ inline void s_pair(const Blk B, rr_instance *inst, JobWS *wsv, int co
     int nrecv = 0, nev = 0;
     const int16_t *allRows = ws.atomRows;
     for (int iter = 0; nneg > 0; ++iter) {
-        if (iter > n) { if (lane == 0) I->status = RR_ERR_TIMEOUT; return; }
+        if (iter > n || (g_guard_cap > 0 && iter >= g_guard_cap)) { if (lane == 0) I->status = RR_ERR_TIMEOUT; return; }
         unsigned long long best = 0ull;
         for (int c = lane; c < n; c += 32) { const unsigned long long s = S.score[c]; best = s > best ? s : best; }
         best = warp_max_u64(best);
