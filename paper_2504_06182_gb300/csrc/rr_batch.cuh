@@ -1462,4 +1462,236 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
     }
 }
 
+// ------------------------------------------------- small-grid simulation
+//
+// Alg. 4 for one small instance with the ready set in warp registers. At most
+// SMALL_CAP moves may be ready at once: two per lane, slot j = 32 p + lane of
+// plane p, kept sorted by move id, so that slot 0 holds the leader (the
+// lowest unfinished id) and a ballot in slot order lists candidates in id
+// order. Every segment is recomputed from the registers: the batch is the
+// leader plus every ready move of its direction on its row (set A) or on its
+// column (set B), whichever holds the lower id (the same rule as sim_body);
+// the segment ends at the first leg end of a batch move or where the leader
+// reaches a row (vertical moves) or column (horizontal ones) holding a ready
+// move of its direction. Finishing moves release their successors (in-degrees
+// in shared memory) and the ready set is re-sorted through shared memory.
+// The move records are staged in shared memory first. An instance with more
+// than SMALL_MAX_MOVES moves, or more than SMALL_CAP ready at once, is left to
+// sim_body (status RR_SIM_RETRY: its wide pass redoes it from the start).
+constexpr int SMALL_CAP = 64;
+constexpr int SMALL_MAX_MOVES = 2048;
+constexpr int SMALL_SBUF = 128;   // successor entries released per round
+
+__host__ __device__ inline size_t small_smem_bytes()
+{
+    return 32ull * SMALL_MAX_MOVES + 4ull * SMALL_MAX_MOVES +      // records, in-degrees
+           16ull * SMALL_CAP + 4ull * SMALL_CAP +                  // re-sort staging, sorted survivor ids
+           4ull * (SMALL_CAP + 32) + 4ull * SMALL_SBUF + 4ull * (SMALL_CAP + 2);   // new ids, successors, batch
+}
+
+struct SmallSlot { int32_t id, key, rem, dst; };
+
+__device__ __forceinline__ SmallSlot small_from_rec(int id, int4 r)
+{
+    const int sr = r.x & 0xffff, sc = r.x >> 16, dr = r.y & 0xffff, dc = r.y >> 16;
+    const int d = dc != sc ? (dc > sc ? 3 : 2) : (dr > sr ? 1 : 0);
+    return SmallSlot{id, key_of(sr, sc, d), dc != sc ? iabs(dc - sc) : iabs(dr - sr), dr};
+}
+
+// Returns with I->status unchanged (done), RR_SIM_RETRY (left to sim_body) or
+// an error status. One warp; `sm` is this warp's shared memory.
+__device__ inline void sim_small(rr_instance *I, JobWS &ws, char *sm)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    if (!live(I)) return;
+    const int k = (int)I->n_moves;
+    if (k == 0) { if (lane == 0) { I->n_ops = 0; I->n_members = 0; } return; }
+    if (k > SMALL_MAX_MOVES) { if (lane == 0) I->status = RR_SIM_RETRY; return; }
+    int4 *recs = (int4 *)sm;                                   // 2 per move: geometry, first successors
+    int32_t *indeg = (int32_t *)(recs + 2 * SMALL_MAX_MOVES);
+    SmallSlot *stage = (SmallSlot *)(indeg + SMALL_MAX_MOVES);
+    int32_t *survIds = (int32_t *)(stage + SMALL_CAP);
+    int32_t *newIds = survIds + SMALL_CAP;
+    int32_t *sbuf = newIds + SMALL_CAP + 32;
+    int32_t *bat = sbuf + SMALL_SBUF;
+    for (int i = lane; i < 2 * k; i += 32) recs[i] = ws.rec[i];
+    for (int i = lane; i < k; i += 32) indeg[i] = ws.indeg[i];
+    __syncwarp();
+
+    // the initially ready moves, sorted by id
+    const int n0 = ws.ready0[k];
+    if (n0 > SMALL_CAP) { if (lane == 0) I->status = RR_SIM_RETRY; return; }
+    for (int i = lane; i < n0; i += 32) newIds[i] = ws.ready0[i];
+    __syncwarp();
+    SmallSlot S0{INTMAX, 0, 0, 0}, S1{INTMAX, 0, 0, 0};
+    for (int i = lane; i < n0; i += 32) {
+        const int id = newIds[i];
+        int r = 0;
+        for (int j = 0; j < n0; ++j) r += newIds[j] < id;
+        stage[r] = small_from_rec(id, recs[2 * id]);
+    }
+    __syncwarp();
+    if (lane < n0) S0 = stage[lane];
+    if (32 + lane < n0) S1 = stage[32 + lane];
+    __syncwarp();
+
+    const int64_t cap_ops = I->cap_ops, cap_mem = I->cap_members;
+    rr_op *ops = I->ops;
+    int32_t *mem = I->members;
+    int64_t nop = 0, nmem = 0;
+    int overflow = 0, err = 0, done = 0;
+    const int64_t guard_max = g_guard_cap > 0 ? g_guard_cap : I->n_steps + 2ll * k + 16;
+    for (int64_t guard = 0;; ++guard) {
+        if (guard >= guard_max) { err = RR_ERR_TIMEOUT; break; }
+        const int Lid = __shfl_sync(FULL, S0.id, 0);
+        if (Lid == INTMAX) break;
+        const int Lkey = __shfl_sync(FULL, S0.key, 0);
+        const int d = key_d(Lkey), lr = key_r(Lkey), lc = key_c(Lkey);
+        const bool vert = d < 2;
+        const int sgn = (d == 1 || d == 3) ? 1 : -1;
+        // candidates: ready moves of direction d, the leader excluded
+        const bool same0 = S0.id != INTMAX && key_d(S0.key) == d && lane != 0;
+        const bool same1 = S1.id != INTMAX && key_d(S1.key) == d;
+        const unsigned bR0 = __ballot_sync(FULL, same0 && key_r(S0.key) == lr);
+        const unsigned bC0 = __ballot_sync(FULL, same0 && key_c(S0.key) == lc);
+        const unsigned bR1 = __ballot_sync(FULL, same1 && key_r(S1.key) == lr);
+        const unsigned bC1 = __ballot_sync(FULL, same1 && key_c(S1.key) == lc);
+        unsigned m0 = 0u, m1 = 0u;
+        if (bR0 | bC0) {
+            const int f = __ffs(bR0 | bC0) - 1;
+            const bool row = (bR0 >> f) & 1u;
+            m0 = row ? bR0 : bC0;
+            m1 = row ? bR1 : bC1;
+        } else if (bR1 | bC1) {
+            const int f = __ffs(bR1 | bC1) - 1;
+            const bool row = (bR1 >> f) & 1u;
+            m1 = row ? bR1 : bC1;
+        }
+        const bool in0 = lane == 0 || ((m0 >> lane) & 1u), in1 = (m1 >> lane) & 1u;
+        const int ns = 1 + __popc(m0) + __popc(m1);
+        // segment length: the first leg end in the batch, the nearest ready
+        // move of direction d on a line ahead of the leader
+        auto limit = [&](const SmallSlot &S, bool inB, bool same) {
+            if (inB) return S.rem;
+            if (same) {
+                const int dist = (vert ? key_r(S.key) - lr : key_c(S.key) - lc) * sgn;
+                if (dist > 0) return dist;
+            }
+            return INTMAX;
+        };
+        const int kseg = __reduce_min_sync(FULL, min(limit(S0, in0, same0), limit(S1, in1, same1)));
+        if (kseg < 1 || kseg == INTMAX) { err = RR_ERR_INTERNAL; break; }
+        // kseg identical batches: ids in rank order (leader first, then slot order)
+        const int64_t addm = (int64_t)kseg * ns;
+        if (!overflow && nop + kseg <= cap_ops && nmem + addm <= cap_mem) {
+            for (int i = lane; i < kseg; i += 32) ops[nop + i] = rr_op{d, (int32_t)(nmem + (int64_t)i * ns), ns};
+            // the batch's ids in rank order: the leader, then the members in
+            // slot (id) order
+            if (in0) bat[lane == 0 ? 0 : 1 + __popc(m0 & lt)] = S0.id;
+            if (in1) bat[1 + __popc(m0) + __popc(m1 & lt)] = S1.id;
+            __syncwarp();
+            if (ns <= 32) {
+                // lane r writes the r-th member of every batch of the segment
+                const int v = lane < ns ? bat[lane] : 0;
+                if (lane < ns)
+                    for (int i = 0; i < kseg; ++i) mem[nmem + (int64_t)i * ns + lane] = v;
+                __syncwarp();
+            } else {
+                int u = small_mod(lane, ns);
+                const int step = small_mod(32, ns);
+                for (int64_t i = lane; i < addm; i += 32) {
+                    mem[nmem + i] = bat[u];
+                    u += step;
+                    if (u >= ns) u -= ns;
+                }
+                __syncwarp();
+            }
+        } else {
+            overflow = 1;
+        }
+        nop += kseg;
+        nmem += addm;
+        // advance the batch; at a leg end a move turns toward its
+        // destination row or finishes there
+        bool fin0 = false, fin1 = false;
+        auto advance = [&](SmallSlot &S, bool inB) {
+            if (!inB) return false;
+            int r = key_r(S.key), c = key_c(S.key), dd = key_d(S.key);
+            if (dd == 0) r -= kseg; else if (dd == 1) r += kseg; else if (dd == 2) c -= kseg; else c += kseg;
+            S.rem -= kseg;
+            if (S.rem == 0) {
+                if (r == S.dst) { S.key = key_of(r, c, dd); return true; }
+                dd = S.dst > r ? 1 : 0;
+                S.rem = iabs(S.dst - r);
+            }
+            S.key = key_of(r, c, dd);
+            return false;
+        };
+        fin0 = advance(S0, in0);
+        fin1 = advance(S1, in1);
+        const unsigned f0 = __ballot_sync(FULL, fin0), f1 = __ballot_sync(FULL, fin1);
+        if (!(f0 | f1)) continue;
+        done += __popc(f0) + __popc(f1);
+        // release the finished moves' successors, one finished move at a time
+        // (lane e takes successor e); newly ready ids go to newIds
+        int nn = 0;
+        for (unsigned fm0 = f0, fm1 = f1; fm0 | fm1;) {
+            int src, pl;
+            if (fm0) { src = __ffs(fm0) - 1; fm0 &= fm0 - 1; pl = 0; }
+            else { src = __ffs(fm1) - 1; fm1 &= fm1 - 1; pl = 1; }
+            const int a0 = __shfl_sync(FULL, S0.id, src), a1 = __shfl_sync(FULL, S1.id, src);
+            const int fid = pl ? a1 : a0;
+            const int4 g = recs[2 * fid];
+            const int32_t *s4 = (const int32_t *)&recs[2 * fid + 1];
+            for (int e0 = 0; e0 < g.z; e0 += 32) {
+                const int e = e0 + lane;
+                int ready = -1;
+                if (e < g.z) {
+                    const int v = e < 4 ? s4[e] : ws.succ[g.w + e - 4];
+                    const int sid = v & SUCC_ID;
+                    if ((v & SUCC_SINGLE) || atomicSub(&indeg[sid], 1) == 1) ready = sid;
+                }
+                const unsigned bal = __ballot_sync(FULL, ready >= 0);
+                if (ready >= 0 && nn + __popc(bal & lt) < 32) newIds[nn + __popc(bal & lt)] = ready;
+                nn += __popc(bal);
+            }
+        }
+        // the ready set again, sorted: survivors keep their order, newly ready
+        // moves go between them by id
+        const bool sv0 = S0.id != INTMAX && !fin0, sv1 = S1.id != INTMAX && !fin1;
+        const unsigned b0v = __ballot_sync(FULL, sv0), b1v = __ballot_sync(FULL, sv1);
+        const int nsv = __popc(b0v) + __popc(b1v);
+        if (nn > 32 || nsv + nn > SMALL_CAP) { if (lane == 0) I->status = RR_SIM_RETRY; return; }
+        __syncwarp();
+        const int myNew = lane < nn ? newIds[lane] : INTMAX;
+        int c0 = 0, c1 = 0, posNew = 0;
+        for (int t = 0; t < nn; ++t) {
+            const int id = __shfl_sync(FULL, myNew, t);
+            const int below = __popc(__ballot_sync(FULL, sv0 && S0.id < id)) +
+                              __popc(__ballot_sync(FULL, sv1 && S1.id < id)) +
+                              __popc(__ballot_sync(FULL, myNew < id));
+            if (lane == t) posNew = below;
+            c0 += sv0 && id < S0.id;
+            c1 += sv1 && id < S1.id;
+        }
+        if (sv0) stage[__popc(b0v & lt) + c0] = S0;
+        if (sv1) stage[__popc(b0v) + __popc(b1v & lt) + c1] = S1;
+        if (lane < nn) stage[posNew] = small_from_rec(myNew, recs[2 * myNew]);
+        __syncwarp();
+        const int T = nsv + nn;
+        S0 = lane < T ? stage[lane] : SmallSlot{INTMAX, 0, 0, 0};
+        S1 = 32 + lane < T ? stage[32 + lane] : SmallSlot{INTMAX, 0, 0, 0};
+        __syncwarp();
+    }
+    if (lane == 0) {
+        I->n_ops = nop;
+        I->n_members = nmem;
+        if (err) I->status = err;
+        else if (done != k || nmem != I->n_steps) I->status = RR_ERR_INTERNAL;
+        else if (overflow) I->status = RR_ERR_CAPACITY;
+    }
+}
+
+
 } // namespace rrk

@@ -11,6 +11,8 @@
 // grid-stride loop covers all of its work with this block's warps; the
 // single-warp stages (pairing, simulation) run on warp 0 and the two-warp
 // bird stage on warps 0-1 while the other warps wait at the next barrier.
+// The simulation keeps the ready set in registers (sim_small) while it stays
+// within SMALL_CAP moves and falls back to the general one otherwise.
 // The descriptor comes in as a kernel parameter and the final one is written
 // to mapped host memory, so a call is one launch and one synchronisation.
 #include <algorithm>
@@ -23,6 +25,7 @@ namespace rrk {
 __global__ void __launch_bounds__(ONE_THREADS) k_one(rr_instance h, rr_instance *I, JobWS *ws, Arena A, int flags,
                                                       int side, int P2, rr_instance *hostOut)
 {
+    extern __shared__ int4 one_smem[];
     const Blk B{0, 0, 1};
     const int wid = threadIdx.x >> 5;
     const bool bird = (flags & RR_BIRD) != 0, batch = (flags & RR_WITH_BATCH) != 0;
@@ -68,11 +71,21 @@ __global__ void __launch_bounds__(ONE_THREADS) k_one(rr_instance h, rr_instance 
         __syncthreads();
         s_brec(B, I, ws, 1);
         __syncthreads();
-        const int slotCap = 2 * side + 8, lineCap = side;
-        if (wid == 0) sim_body<int16_t, false>(B, I, ws, 1, nullptr, nullptr, slotCap, lineCap);
+        // the ready set in registers when it stays small; else the general
+        // simulation (narrow pass, then the wide one if that runs out of slots)
+        if (wid == 0) sim_small(I, ws[0], (char *)one_smem);
         __syncthreads();
-        if (wid == 0) sim_body<int16_t, true>(B, I, ws, 1, nullptr, nullptr, slotCap, lineCap);
+        const bool general = I->status == RR_SIM_RETRY;
         __syncthreads();
+        if (general) {
+            if (threadIdx.x == 0) I->status = RR_OK;
+            __syncthreads();
+            const int slotCap = 2 * side + 8, lineCap = side;
+            if (wid == 0) sim_body<int16_t, false>(B, I, ws, 1, nullptr, nullptr, slotCap, lineCap);
+            __syncthreads();
+            if (wid == 0) sim_body<int16_t, true>(B, I, ws, 1, nullptr, nullptr, slotCap, lineCap);
+            __syncthreads();
+        }
     }
     if (threadIdx.x < sizeof(rr_instance) / 4) ((volatile int32_t *)hostOut)[threadIdx.x] = ((int32_t *)I)[threadIdx.x];
 }
@@ -95,6 +108,7 @@ size_t one_smem_bytes(int side, int flags)
         b = std::max(b, warps * 4 * (size_t)P2);                              // k_gsort
         b = std::max(b, warps * 12 * (size_t)side);                           // k_gsweep_v (h needs a third)
         b = std::max(b, sim_smem_bytes(2 * side + 8, side, 2));
+        b = std::max(b, small_smem_bytes());
     }
     return b;
 }

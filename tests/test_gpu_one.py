@@ -128,3 +128,16 @@ def test_one_capacity_and_arguments(ctx):
     assert rr.rr_plan_one(ctx, g, rr.RR_U8, 48, 48, inst.rect, 1 << 9, out, 4)[0] == rr.RR_ERR_ARG
     # the context stays usable: a full call after the refusals
     check(ctx, inst.grid, inst.rect, rr.RR_U8)
+
+
+@pytest.mark.parametrize("n", [64, 65, 70])
+def test_one_ready_set_beyond_registers(ctx, n):
+    """Every column starts with a ready move (4 atoms over 4 band rows, full
+    width): n moves ready at once. Up to 64 the simulation keeps them in
+    registers; beyond, the general simulation takes over; the batches are
+    the oracle's either way."""
+    import paper_2504_06182_gb300 as rr
+    grid = np.zeros((8, n), np.uint8)
+    grid[:4] = 1
+    ref = check(ctx, grid, (4, 0, 8, n), rr.RR_U8)
+    assert ref.status == 0 and len(ref.moves) == 4 * n
