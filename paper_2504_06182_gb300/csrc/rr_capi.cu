@@ -379,7 +379,7 @@ static int launch_batch(rr_ctx *ctx, rr_instance *d_inst, JobWS *ws, int count, 
         ctx->nlaunch += 1;
     }
     {
-        // Gamma by column and row sweeps (per-vertex lists only where they fail)
+        // Gamma by column and row sweeps
         const int lineBlocks = clampi(std::max(1, budget(ctx, 8192) / count), 1, (2 * max_side + 7) / 8);
         mark(ctx, s, "k_gcount");
         k_gcount<<<dim3(pathBlocks, count), 256, 0, s>>>(d_inst, ws, count);
