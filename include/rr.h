@@ -7,8 +7,13 @@
  * III.D) and the batching routine (Alg. 4 with the local constraint set of
  * Sec. IV). All arithmetic is integer.
  *
- * Memory: every buffer argument named d_* is caller-owned DEVICE memory; the
- * library never frees or retains it. Host pointers (n_moves, n_ops, ...) are
+ * Memory: every buffer argument named d_* is caller-owned memory the device
+ * can address, normally device memory; the library never frees or retains it.
+ * Output buffers may also be host memory mapped for the device (pinned with
+ * cudaHostAlloc / cudaHostRegister): the kernels then write the results
+ * straight into host memory, with no separate copy. The batching kernels read
+ * the move list several times, so it is best kept in device memory; batches
+ * and members are only written. Host pointers (n_moves, n_ops, ...) are
  * written before the call returns. Workspace lives in the context.
  * Streams: work is issued on `stream`; calls that return counts to host
  * pointers synchronise that stream before returning.
