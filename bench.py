@@ -693,8 +693,10 @@ def run_ours(args, rank, world, local):
     rr.rr_set_tracing(P.ctx, False)
     elapsed_ms = max_over_ranks(sum(times), dev, world)
 
-    # the same step replayed from a captured CUDA graph (RR_GRAPH)
+    # the same step replayed from a captured CUDA graph (RR_GRAPH), under the
+    # configuration the autotuner picks for replays
     gflags = rr.RR_WITH_BATCH | rr.RR_GRAPH
+    graph_cfg = None if args.no_autotune else rr.rr_autotune(P.ctx, d_inst, count, max_side, gflags, stream)
     if rr.rr_plan_batched(P.ctx, d_inst, count, max_side, gflags, stream) != rr.RR_OK:
         raise rr.RRError(-3, rr.rr_last_error(P.ctx))
     torch.cuda.synchronize()
@@ -826,6 +828,8 @@ def run_ours(args, rank, world, local):
                         "written by the kernels into pinned host memory, D2H of the moves and descriptors"},
         "gpu_launches": launches,
         "graph": {"value": count * args.steps / (graph_total * 1e-3), "unit": "grids/s",
+                  "autotuned_for_replay": None if graph_cfg is None else
+                  {"size_classes": graph_cfg[0], "block_budget_scale": 2.0 ** graph_cfg[1], "split": graph_cfg[2]},
                   "note": "same step replayed from one captured CUDA graph (RR_GRAPH), inputs resident"},
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -195,7 +195,10 @@ int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, i
  * split) when those are not NULL. Every
  * configuration computes the same results, so the descriptors and outputs
  * hold this call's results afterwards. Synchronises; flags as
- * rr_plan_batched without RR_GRAPH.
+ * rr_plan_batched. With RR_GRAPH each configuration is captured as a graph
+ * and timed by its replays, so the choice suits later RR_GRAPH calls (the
+ * fastest configuration for direct launches can replay a few percent slower
+ * than another one).
  *
  * Pipeline (batched calls with batching over at least 256 grids): the grids
  * are ordered by side, largest first, into a descriptor copy; each leading

@@ -703,11 +703,36 @@ extern "C" int rr_plan_batched(rr_ctx *ctx, rr_instance *d_inst, int count, int 
     return RR_OK;
 }
 
+// One configuration's time for rr_autotune: the best of two runs of the
+// call's launch sequence, or with RR_GRAPH the best of two replays of the
+// graph captured under that configuration.
+static int tune_time(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags, cudaStream_t stream,
+                     cudaEvent_t a, cudaEvent_t b, float *best)
+{
+    int st = RR_OK;
+    *best = 1e30f;
+    if (flags & RR_GRAPH) {
+        drop_graph(ctx);
+        st = rr_plan_batched(ctx, d_inst, count, max_side, flags, stream);      // capture, then the first replay
+    }
+    for (int rep = 0; rep < 2 && st == RR_OK; ++rep) {
+        cudaEventRecord(a, stream);
+        st = (flags & RR_GRAPH) ? rr_plan_batched(ctx, d_inst, count, max_side, flags, stream)
+                                : launch_sequence(ctx, d_inst, count, max_side, flags, stream);
+        cudaEventRecord(b, stream);
+        if (st == RR_OK && cudaEventSynchronize(b) != cudaSuccess)
+            st = fail(ctx, RR_ERR_CUDA, "rr_autotune: %s", cudaGetErrorString(cudaGetLastError()));
+        float ms = 0.f;
+        if (st == RR_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) *best = std::min(*best, ms);
+    }
+    return st;
+}
+
 extern "C" int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_side, int flags,
                            cudaStream_t stream, int32_t *nclass, int32_t *shift, int32_t *pipe)
 {
     if (!ctx || !d_inst || count < 1 || count > 65535 || max_side < 1 || max_side > RR_MAX_SIDE ||
-        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY | RR_BIRD | RR_STRICT_RESERVOIR)))
+        (flags & ~(RR_WITH_BATCH | RR_BATCH_ONLY | RR_GRAPH | RR_BIRD | RR_STRICT_RESERVOIR)))
         return fail(ctx, RR_ERR_ARG, "rr_autotune: bad argument (count=%d max_side=%d flags=%d)", count, max_side,
                     flags);
     int st = ensure_ws(ctx, count);
@@ -724,15 +749,7 @@ extern "C" int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
         ctx->nclass = NC[i / 3];
         ctx->shift = SH[i % 3];
         float t = 1e30f;
-        for (int rep = 0; rep < 2 && st == RR_OK; ++rep) {     // best of two
-            cudaEventRecord(a, stream);
-            st = launch_sequence(ctx, d_inst, count, max_side, flags, stream);
-            cudaEventRecord(b, stream);
-            if (st == RR_OK && cudaEventSynchronize(b) != cudaSuccess)
-                st = fail(ctx, RR_ERR_CUDA, "rr_autotune: %s", cudaGetErrorString(cudaGetLastError()));
-            float ms = 0.f;
-            if (st == RR_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) t = std::min(t, ms);
-        }
+        st = tune_time(ctx, d_inst, count, max_side, flags, stream, a, b, &t);
         if (t < best) { best = t; bestN = ctx->nclass; bestS = ctx->shift; }
     }
     // then the pipeline split under that configuration
@@ -743,15 +760,7 @@ extern "C" int rr_autotune(rr_ctx *ctx, rr_instance *d_inst, int count, int max_
     for (int i = 0; i < PIPE_SPLITS && st == RR_OK; ++i) {
         ctx->pipe = i;
         float t = 1e30f;
-        for (int rep = 0; rep < 2 && st == RR_OK; ++rep) {
-            cudaEventRecord(a, stream);
-            st = launch_sequence(ctx, d_inst, count, max_side, flags, stream);
-            cudaEventRecord(b, stream);
-            if (st == RR_OK && cudaEventSynchronize(b) != cudaSuccess)
-                st = fail(ctx, RR_ERR_CUDA, "rr_autotune: %s", cudaGetErrorString(cudaGetLastError()));
-            float ms = 0.f;
-            if (st == RR_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) t = std::min(t, ms);
-        }
+        st = tune_time(ctx, d_inst, count, max_side, flags, stream, a, b, &t);
         if (t < best) { best = t; bestP = ctx->pipe; }
     }
     ctx->pipe = bestP;

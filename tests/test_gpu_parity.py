@@ -497,3 +497,45 @@ def load_digests():
 def sha256_i32(a) -> str:
     import hashlib
     return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
+
+
+def test_autotune_for_graph_replay(planner):
+    """rr_autotune with RR_GRAPH times every configuration by graph replays;
+    its results, and a later replay under the configuration it keeps, equal
+    the oracle's."""
+    import paper_2504_06182_gb300 as rr
+    from paper_2504_06182_gb300.planner import pack_instances, unpack_instances
+    insts = gridgen.mixed_instances(14, 24)
+    refs = [oracle.plan(i.grid, i.rect) for i in insts]
+    entries, outs = [], []
+    for inst, ref in zip(insts, refs):
+        s = inst.grid.shape[0]
+        k = max(len(ref.moves), 1)
+        steps = max(1, int((np.abs(ref.moves[:, 0] - ref.moves[:, 2]) +
+                            np.abs(ref.moves[:, 1] - ref.moves[:, 3])).sum()) if len(ref.moves) else 1)
+        mv = torch.empty((k, 4), dtype=torch.int32, device="cuda")
+        ops = torch.empty((steps, 3), dtype=torch.int32, device="cuda")
+        mem = torch.empty((steps,), dtype=torch.int32, device="cuda")
+        entries.append(dict(grid=to_device(inst.grid, rr.RR_BITS32), layout=rr.RR_BITS32, m=s, n=s, rect=inst.rect,
+                            moves=mv, cap_moves=k, ops=ops, cap_ops=steps, members=mem, cap_members=steps))
+        outs.append((mv, ops, mem))
+    dev = pack_instances(entries)
+    flags = rr.RR_WITH_BATCH | rr.RR_GRAPH
+    rr.rr_autotune(planner.ctx, dev, len(entries), 256, flags)
+    for call in range(2):
+        if call == 1:
+            for t in outs:
+                for x in t:
+                    x.zero_()
+            assert rr.rr_plan_batched(planner.ctx, dev, len(entries), 256, flags) == rr.RR_OK
+        torch.cuda.synchronize()
+        for inst, ref, r, (mv, ops, mem) in zip(insts, refs, unpack_instances(dev, len(entries)), outs):
+            assert r.status == (rr.RR_OK if ref.status == 0 else rr.RR_INFEASIBLE)
+            assert r.n_moves == len(ref.moves)
+            if ref.status != 0:
+                continue
+            assert (mv[: r.n_moves].cpu().numpy() == ref.moves).all()
+            rops, rmem = oracle.batch(ref.moves, *inst.grid.shape)
+            assert (ops[: r.n_ops].cpu().numpy() == rops).all() and r.n_ops == len(rops)
+            assert (mem[: r.n_members].cpu().numpy() == rmem).all() and r.n_members == len(rmem)
+    rr.rr_set_config(planner.ctx, 4, 0, 1)
