@@ -995,6 +995,108 @@ __device__ void dissolve(const S &X, int nm, bool rowLine)
     __syncwarp();
 }
 
+// The leader (the lowest unfinished move, which is always ready) lives in
+// warp-uniform registers and holds no slot: its key (position, direction),
+// steps done, the end of its current leg, its destination row, and the
+// successor part of its record (count, overflow offset, first four), loaded
+// when it becomes the leader so that the load has long completed when it
+// finishes.
+struct LeaderState {
+    int key = 0, t = 0, legEnd = 0, dstRow = 0, nsu = 0, ov = 0;
+    int4 s4 = {-1, -1, -1, -1};
+    bool pref = false;   // its successors' records still to be prefetched
+};
+
+// A ready move becomes the leader: its state moves from its slot (already
+// out of the lists and the members) into the registers and the slot is freed.
+template <class S>
+__device__ __forceinline__ void leader_from_slot(const S &X, const JobWS &ws, int si, int &L, LeaderState &Ld,
+                                                 int &freeTop, int &ovfFreeTop)
+{
+    using IX = typename S::ix;
+    const int lane = threadIdx.x & 31;
+    L = SLOTF(X, id, si);
+    Ld.key = SLOTF(X, key, si) & ~KEY_MEM;
+    Ld.t = SLOTF(X, t, si);
+    Ld.legEnd = SLOTF(X, legEnd, si);
+    Ld.dstRow = SLOTF(X, dstRow, si);
+    const int4 own = ws.rec[2 * L];
+    Ld.s4 = ws.rec[2 * L + 1];
+    Ld.nsu = own.z;
+    Ld.ov = own.w;
+    Ld.pref = true;
+    __syncwarp();
+    if (lane == 0) {
+        if (X.map[L & (MAPN - 1)] == si) X.map[L & (MAPN - 1)] = -1;
+        SLOTF(X, key, si) = 0;
+        SLOTF(X, id, si) = INTMAX;
+        if (si < X.C) X.freeStk[freeTop] = (int16_t)si; else X.ovfFree[ovfFreeTop] = si;
+    }
+    if (si < X.C) ++freeTop; else ++ovfFreeTop;
+    __syncwarp();
+}
+
+// A move that became ready just now becomes the leader straight from its
+// record (the first leg as fill_slot sets it).
+__device__ __forceinline__ void leader_from_rec(const JobWS &ws, int id, int4 r, int &L, LeaderState &Ld)
+{
+    const int sr = r.x & 0xffff, sc = r.x >> 16, dr = r.y & 0xffff, dc = r.y >> 16;
+    const int d = dc != sc ? (dc > sc ? 3 : 2) : (dr > sr ? 1 : 0);
+    L = id;
+    Ld.key = key_of(sr, sc, d);
+    Ld.t = 0;
+    Ld.legEnd = dc != sc ? iabs(dc - sc) : iabs(dr - sr);
+    Ld.dstRow = dr;
+    Ld.nsu = r.z;
+    Ld.ov = r.w;
+    Ld.s4 = ws.rec[2 * id + 1];
+    Ld.pref = true;
+}
+
+// One round of successor entries, at most one per lane (warp-cooperative):
+// e is a flagged successor id, or ~index into the successor array. Each
+// entry decrements its move's in-degree (unless the move has no other
+// predecessor); moves that become ready take a slot and join the static
+// lists, except the move handId (the next leader once the leader has
+// finished), whose record is handed back in handRec with hand set.
+template <class S>
+__device__ __forceinline__ void release_round(const S &X, const JobWS &ws, bool has, int32_t e, int handId,
+                                              int &hand, int4 &handRec, int &freeTop, int &ovfFreeTop,
+                                              int &ovfUsed, int &hi, int kmax, int *err)
+{
+    using IX = typename S::ix;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int ready = -1;
+    int4 r = make_int4(0, 0, 0, 0);
+    if (has) {
+        if (e < 0) e = ws.succ[~e];
+        const int id = e & SUCC_ID;
+        r = ws.rec[2 * id];   // fetched with the counter update
+        if ((e & SUCC_SINGLE) || atomicSub(&ws.indeg[id], 1) == 1) ready = id;
+    }
+    const unsigned hb = __ballot_sync(FULL, ready >= 0 && ready == handId);
+    if (hb) {
+        const int src = __ffs(hb) - 1;
+        handRec.x = __shfl_sync(FULL, r.x, src);
+        handRec.y = __shfl_sync(FULL, r.y, src);
+        handRec.z = __shfl_sync(FULL, r.z, src);
+        handRec.w = __shfl_sync(FULL, r.w, src);
+        hand = 1;
+        if (lane == src) ready = -1;
+    }
+    const unsigned bal = __ballot_sync(FULL, ready >= 0);
+    const int cnt = __popc(bal);
+    if (cnt) {
+        const int si = alloc_slot(X, __popc(bal & lt), cnt, freeTop, ovfFreeTop, ovfUsed, hi, kmax, err);
+        int key = 0;
+        if (ready >= 0 && si >= 0) key = fill_slot(X, si, ready, r);
+        __syncwarp();
+        push_lanes(X, __ballot_sync(FULL, ready >= 0 && si >= 0), si, key);
+    }
+    __syncwarp();
+}
+
 // Instance order by side, largest first: a counting sort on max(m, n)
 // (one block; positions within a side follow the atomics, which does not
 // matter: instances are independent). perm[i] is the instance at position i.
@@ -1159,12 +1261,15 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
     int overflow = 0;
     int Ls = lowest_slot(X, hi);
     int L = Ls >= 0 ? SLOTF(X, id, Ls) : -1;
+    // the leader: warp-uniform registers, no slot (see LeaderState)
+    LeaderState Ld;
     if (err) {
         // out of slots already (narrow pass): handed to the wide pass
     } else if (L != 0) err = RR_ERR_INTERNAL;
     else {
         if (lane == 0) { const int kk = SLOTF(X, key, Ls); unlink_row(X, Ls, kk); unlink_col(X, Ls, kk); }
         __syncwarp();
+        leader_from_slot(X, ws, Ls, L, Ld, freeTop, ovfFreeTop);
     }
     // members: nm of them (leader excluded), on one line of type rowLine at
     // index lineIdx, direction dm
@@ -1175,26 +1280,27 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
 
     while (!err && L < k) {
         if (++guard > guard_max) { err = RR_ERR_TIMEOUT; break; }
-        // the leader's position and direction are in its key (kept current)
-        const int kL = SLOTF(X, key, Ls);
-        const int lr = key_r(kL), lc = key_c(kL), d = key_d(kL);
-        const int remL = SLOTF(X, legEnd, Ls) - SLOTF(X, t, Ls);
+        const int lr = key_r(Ld.key), lc = key_c(Ld.key), d = key_d(Ld.key);
+        const int remL = Ld.legEnd - Ld.t;
         const int sgn = (d == 1 || d == 3) ? 1 : -1;
         // members still on the leader's line in the leader's direction?
         if (nm > 0 && !(dm == d && (rowLine ? lineIdx == lr : lineIdx == lc))) { dissolve(X, nm, rowLine); nm = 0; }
-        // smallest static id on the leader's row and column (lane 0 walks)
+        // smallest static id on the leader's row and column (lane 0 walks;
+        // nothing to walk when both lists are empty)
         int minA = INTMAX, minB = INTMAX;
         const int hA = X.rowHead[d * m + lr], hB = X.colHead[d * n + lc];
-        if (lane == 0) {
-            int walk = 0;
-            for (int p = hA; p >= 0 && walk <= lineCap; p = SLOTF(X, rn, p), ++walk) minA = min(minA, SLOTF(X, id, p));
-            for (int p = hB; p >= 0 && walk <= 2 * lineCap; p = SLOTF(X, cn, p), ++walk) minB = min(minB, SLOTF(X, id, p));
-            if (walk > 2 * lineCap) err = RR_ERR_INTERNAL;
+        if (hA >= 0 || hB >= 0) {
+            if (lane == 0) {
+                int walk = 0;
+                for (int p = hA; p >= 0 && walk <= lineCap; p = SLOTF(X, rn, p), ++walk) minA = min(minA, SLOTF(X, id, p));
+                for (int p = hB; p >= 0 && walk <= 2 * lineCap; p = SLOTF(X, cn, p), ++walk) minB = min(minB, SLOTF(X, id, p));
+                if (walk > 2 * lineCap) err = RR_ERR_INTERNAL;
+            }
+            minA = __shfl_sync(FULL, minA, 0);
+            minB = __shfl_sync(FULL, minB, 0);
+            err = __shfl_sync(FULL, err, 0);
+            if (err) break;
         }
-        minA = __shfl_sync(FULL, minA, 0);
-        minB = __shfl_sync(FULL, minB, 0);
-        err = __shfl_sync(FULL, err, 0);
-        if (err) break;
         if (nm > 0) { if (rowLine) minA = min(minA, X.Mid[0]); else minB = min(minB, X.Mid[0]); }
         // records of up to 32 newcomers: fetched when they join, their
         // successors' records prefetched once the segment is emitted
@@ -1284,9 +1390,11 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
         }
         // segment length: shortest remaining leg, next pickup
         int kseg = remL;
-        int remM = INTMAX;
-        for (int u = lane; u < nm; u += 32) { const int si = X.Msl[u]; remM = min(remM, SLOTF(X, legEnd, si) - SLOTF(X, t, si)); }
-        kseg = min(kseg, __reduce_min_sync(FULL, remM));   // one warp reduction
+        if (nm > 0) {
+            int remM = INTMAX;
+            for (int u = lane; u < nm; u += 32) { const int si = X.Msl[u]; remM = min(remM, SLOTF(X, legEnd, si) - SLOTF(X, t, si)); }
+            kseg = min(kseg, __reduce_min_sync(FULL, remM));   // one warp reduction
+        }
         if (kseg > 1) {   // a static move of direction d the leader's line reaches
             const int hit = d >= 2 ? bit_scan(X.colBits + (d - 2) * X.Wn, n, lc, sgn, kseg - 1)
                                    : bit_scan(X.rowBits + d * X.Wm, m, lr, sgn, kseg - 1);
@@ -1316,20 +1424,44 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
         nop += kseg;
         nmem += addm;
 
-        // advance: u = 0 is the leader, u >= 1 member u-1. Finished moves
-        // release their successors; members whose leg ended leave the batch
-        // and become statics; the others stay members.
+        // advance by kseg steps along the current legs (no batch move's leg
+        // ends before the segment does); at a leg's end a move finishes on
+        // its destination row or turns toward it. The leader first (its
+        // registers), then the members: finished members release their
+        // successors, members whose leg ended leave the batch and become
+        // statics, the others stay members.
         if (lane < npref) prefetch_succ(ws, ns4, nrec.z);
-        int leaderDone = 0, nkeep = 0;
-        for (int u0 = 0; u0 < ns; u0 += 32) {
+        if (Ld.pref) {   // the leader's record has arrived by now
+            prefetch_succ(ws, Ld.s4, lane == 0 ? Ld.nsu : 0);
+            Ld.pref = false;
+        }
+        bool lfin = false;
+        {
+            const int t = Ld.t + kseg;
+            const int r_ = lr + (d == 1 ? kseg : d == 0 ? -kseg : 0);
+            const int c_ = lc + (d == 3 ? kseg : d == 2 ? -kseg : 0);
+            int d_ = d;
+            Ld.t = t;
+            if (t == Ld.legEnd) {
+                if (r_ == Ld.dstRow) lfin = true;
+                else { d_ = Ld.dstRow > r_ ? 1 : 0; Ld.legEnd = t + iabs(Ld.dstRow - r_); }
+            }
+            Ld.key = key_of(r_, c_, d_);
+        }
+        // once the leader has finished, L + 1 (if it becomes ready now) is the
+        // next leader and takes no slot
+        const int handId = lfin ? L + 1 : -1;
+        int hand = 0;
+        int4 handRec = make_int4(0, 0, 0, 0);
+        int nkeep = 0;
+        for (int u0 = 0; u0 < nm; u0 += 32) {
             const int u = u0 + lane;
-            bool fin = false, turn = false, act = u < ns;
+            bool fin = false, turn = false;
+            const bool act = u < nm;
             int si = -1, nsu = 0, newKey = 0, ov = 0;
             int4 fs4 = make_int4(0, 0, 0, 0);
             if (act) {
-                si = u == 0 ? Ls : X.Msl[u - 1];
-                // kseg steps along the current leg (no batch move's leg ends
-                // before the segment does), then finish or turn at its end
+                si = X.Msl[u];
                 const int key = SLOTF(X, key, si);
                 const int t = SLOTF(X, t, si) + kseg;
                 const int le = SLOTF(X, legEnd, si);
@@ -1351,21 +1483,19 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
                     nsu = own.z;
                     ov = own.w;
                 } else {
-                    turn = u > 0 && d_ != d;
-                    newKey = key_of(r_, c_, d_) | (u > 0 && !turn ? KEY_MEM : 0);
+                    turn = d_ != d;
+                    newKey = key_of(r_, c_, d_) | (turn ? 0 : KEY_MEM);
                     SLOTF(X, key, si) = newKey;
                     if (t + rem != le) SLOTF(X, legEnd, si) = (int16_t)(t + rem);
                 }
             }
-            if (u0 == 0 && __shfl_sync(FULL, (int)fin, 0)) leaderDone = 1;
             // survivors keep their order (stable compaction into Kb)
-            const bool keep = act && u > 0 && !fin && !turn;
+            const bool keep = act && !fin && !turn;
             const unsigned kb = __ballot_sync(FULL, keep);
-            if (keep) X.Kb[nkeep + __popc(kb & lt)] = ((long long)X.Mid[u - 1] << 32) | (unsigned)si;
+            if (keep) X.Kb[nkeep + __popc(kb & lt)] = ((long long)X.Mid[u] << 32) | (unsigned)si;
             nkeep += __popc(kb);
             // members whose leg ended become statics
             push_lanes(X, __ballot_sync(FULL, turn), si, newKey);
-            // successor entries of the finished moves, in rounds of SBUF
             if (!__any_sync(FULL, fin)) continue;     // nothing finished in this chunk
             const int off = warp_incl_scan(nsu) - nsu;
             const int total = __shfl_sync(FULL, off + nsu, 31);
@@ -1384,6 +1514,7 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
             freeTop += __popc(fb);
             ovfFreeTop += __popc(fo);
             __syncwarp();
+            // successor entries of the finished members, in rounds of SBUF
             for (int base = 0; base < total; base += SBUF) {
                 if (fin) {
                     for (int e = max(0, base - off); e < nsu && off + e < base + SBUF; ++e)
@@ -1393,26 +1524,20 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
                 __syncwarp();
                 const int nb = min(SBUF, total - base);
                 for (int b0 = 0; b0 < nb; b0 += 32) {
-                    int ready = -1;
-                    int4 r = make_int4(0, 0, 0, 0);
-                    if (b0 + lane < nb) {
-                        int32_t e = X.sbuf[b0 + lane];
-                        if (e < 0) e = ws.succ[~e];
-                        const int id = e & SUCC_ID;
-                        r = ws.rec[2 * id];   // fetched with the counter update
-                        if ((e & SUCC_SINGLE) || atomicSub(&ws.indeg[id], 1) == 1) ready = id;
-                    }
-                    const unsigned bal = __ballot_sync(FULL, ready >= 0);
-                    const int cnt = __popc(bal);
-                    if (cnt) {
-                        const int ns_ = alloc_slot(X, __popc(bal & lt), cnt, freeTop, ovfFreeTop, ovfUsed, hi, k, &err);
-                        int key = 0;
-                        if (ready >= 0 && ns_ >= 0) key = fill_slot(X, ns_, ready, r);
-                        __syncwarp();
-                        push_lanes(X, __ballot_sync(FULL, ready >= 0 && ns_ >= 0), ns_, key);
-                    }
-                    __syncwarp();
+                    const bool has = b0 + lane < nb;
+                    release_round(X, ws, has, has ? X.sbuf[b0 + lane] : 0, handId, hand, handRec, freeTop,
+                                  ovfFreeTop, ovfUsed, hi, k, &err);
                 }
+            }
+        }
+        // the finished leader's successors, straight from its registers
+        if (lfin) {
+            for (int e0 = 0; e0 < Ld.nsu; e0 += 32) {
+                const int e = e0 + lane;
+                const int32_t v = e == 0 ? Ld.s4.x : e == 1 ? Ld.s4.y : e == 2 ? Ld.s4.z : e == 3 ? Ld.s4.w
+                                                                                            : ~(Ld.ov + e - 4);
+                release_round(X, ws, e < Ld.nsu, v, handId, hand, handRec, freeTop, ovfFreeTop, ovfUsed, hi, k,
+                              &err);
             }
         }
         for (int u = lane; u < nkeep; u += 32) { X.Mid[u] = (int)(X.Kb[u] >> 32); X.Msl[u] = (int)(X.Kb[u] & 0xffffffff); }
@@ -1421,33 +1546,36 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
         if (rowLine && d < 2) lineIdx += sgn * kseg;
         if (!rowLine && d >= 2) lineIdx += sgn * kseg;
         __syncwarp();
-        if (leaderDone && !err) {
-            // next leader: the lowest id still held (usually L + 1); a member
-            // leader leaves the front of the members, a static one its lists
-            int cand = -1;
-            const int nx = L + 1;
-            if (nx < k) {
-                const int si = X.map[nx & (MAPN - 1)];
-                if (si >= 0 && SLOTF(X, id, si) == nx) cand = si;
-            }
-            if (cand < 0) cand = lowest_slot(X, hi);
-            if (cand < 0) L = k;
+        if (lfin && !err) {
+            // next leader: the lowest unfinished id. L + 1, if it became ready
+            // just now, takes over at once; otherwise the lowest id still held
+            // (usually L + 1): a member leaves the front of the members, a
+            // static its lists
+            if (hand) leader_from_rec(ws, L + 1, handRec, L, Ld);
             else {
-                Ls = cand;
-                L = SLOTF(X, id, Ls);
-                if (lane == 0) prefetch_rec(ws, L);
-                const int kk = SLOTF(X, key, Ls);
-                if (kk & KEY_MEM) {
-                    if (nm == 0 || X.Msl[0] != Ls) { err = RR_ERR_INTERNAL; break; }
+                int cand = -1;
+                const int nx = L + 1;
+                if (nx < k) {
+                    const int si = X.map[nx & (MAPN - 1)];
+                    if (si >= 0 && SLOTF(X, id, si) == nx) cand = si;
+                }
+                if (cand < 0) cand = lowest_slot(X, hi);
+                if (cand < 0) L = k;
+                else {
+                    const int kk = SLOTF(X, key, cand);
+                    if (kk & KEY_MEM) {
+                        if (nm == 0 || X.Msl[0] != cand) { err = RR_ERR_INTERNAL; break; }
+                        __syncwarp();
+                        for (int u = lane; u + 1 < nm; u += 32) X.Kb[u] = ((long long)X.Mid[u + 1] << 32) | (unsigned)X.Msl[u + 1];
+                        __syncwarp();
+                        --nm;
+                        for (int u = lane; u < nm; u += 32) { X.Mid[u] = (int)(X.Kb[u] >> 32); X.Msl[u] = (int)(X.Kb[u] & 0xffffffff); }
+                    } else if (lane == 0) {
+                        unlink_row(X, cand, kk);
+                        unlink_col(X, cand, kk);
+                    }
                     __syncwarp();
-                    for (int u = lane; u + 1 < nm; u += 32) X.Kb[u] = ((long long)X.Mid[u + 1] << 32) | (unsigned)X.Msl[u + 1];
-                    __syncwarp();
-                    --nm;
-                    for (int u = lane; u < nm; u += 32) { X.Mid[u] = (int)(X.Kb[u] >> 32); X.Msl[u] = (int)(X.Kb[u] & 0xffffffff); }
-                    if (lane == 0) SLOTF(X, key, Ls) = kk & ~KEY_MEM;
-                } else if (lane == 0) {
-                    unlink_row(X, Ls, kk);
-                    unlink_col(X, Ls, kk);
+                    leader_from_slot(X, ws, cand, L, Ld, freeTop, ovfFreeTop);
                 }
             }
         }
