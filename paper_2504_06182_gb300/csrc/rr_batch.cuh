@@ -820,21 +820,43 @@ __device__ __forceinline__ void push_lanes(const S &X, unsigned pend, int si, in
     }
 }
 
-// First i in 1..maxq with bit (pos + i*delta) set, or 0 (delta = +-1): a
-// word at a time, the nearest set bit found with ffs / clz.
+// First i in 1..maxq with bit (pos + i*delta) set, or 0 (delta = +-1)
+// (warp-uniform arguments; every lane calls it). The bits of the range
+// [lo, hi] are read a word per lane, 32 words (1 024 bits) per round, and
+// the nearest set bit is found with a ballot and ffs / clz; a range within
+// one word needs no vote.
 __device__ inline int bit_scan(const uint32_t *b, int limit, int pos, int delta, int maxq)
 {
-    if (delta > 0) {
-        const int end = min(limit - 1, pos + maxq);
-        for (int x = pos + 1; x <= end; x = (x | 31) + 1) {
-            const uint32_t w = b[x >> 5] & (~0u << (x & 31));
-            if (w) { const int y = (x & ~31) + __ffs(w) - 1; return y <= end ? y - pos : 0; }
-        }
-    } else {
-        const int end = max(0, pos - maxq);
-        for (int x = pos - 1; x >= end; x = (x & ~31) - 1) {
-            const uint32_t w = b[x >> 5] & (0xffffffffu >> (31 - (x & 31)));
-            if (w) { const int y = (x & ~31) + 31 - __clz(w); return y >= end ? pos - y : 0; }
+    const int lane = threadIdx.x & 31;
+    const int lo = delta > 0 ? pos + 1 : max(0, pos - maxq);
+    const int hi = delta > 0 ? min(limit - 1, pos + maxq) : pos - 1;
+    if (lo > hi) return 0;
+    const int w0 = lo >> 5, w1 = hi >> 5;
+    auto masked = [&](int w) {
+        uint32_t v = b[w];
+        if (w == w0) v &= ~0u << (lo & 31);
+        if (w == w1) v &= 0xffffffffu >> (31 - (hi & 31));
+        return v;
+    };
+    if (w0 == w1) {
+        const uint32_t v = masked(w0);
+        if (!v) return 0;
+        const int y = delta > 0 ? (w0 << 5) + __ffs(v) - 1 : (w0 << 5) + 31 - __clz(v);
+        return delta > 0 ? y - pos : pos - y;
+    }
+    const int nw = w1 - w0 + 1;
+    for (int r = 0; r < nw; r += 32) {
+        // rounds run outward from pos: ascending words when delta > 0
+        const int idx = r + lane;
+        const int w = delta > 0 ? w0 + idx : w1 - idx;
+        const uint32_t v = idx < nw ? masked(w) : 0u;
+        const unsigned bal = __ballot_sync(FULL, v != 0u);
+        if (bal) {
+            const int src = __ffs(bal) - 1;   // the word nearest pos
+            const uint32_t vv = __shfl_sync(FULL, v, src);
+            const int ws = delta > 0 ? w0 + r + src : w1 - r - src;
+            const int y = delta > 0 ? (ws << 5) + __ffs(vv) - 1 : (ws << 5) + 31 - __clz(vv);
+            return delta > 0 ? y - pos : pos - y;
         }
     }
     return 0;
@@ -1277,6 +1299,10 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
     bool rowLine = true;
     const int64_t guard_max = g_guard_cap > 0 ? g_guard_cap : I->n_steps + 2ll * k + 16;
     int64_t guard = 0;
+    // records of up to 32 newcomers: fetched when they join, their
+    // successors' records prefetched in the next segment
+    int4 nrec = make_int4(0, 0, 0, 0), ns4 = nrec;
+    int npref = 0;
 
     while (!err && L < k) {
         if (++guard > guard_max) { err = RR_ERR_TIMEOUT; break; }
@@ -1302,10 +1328,10 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
             if (err) break;
         }
         if (nm > 0) { if (rowLine) minA = min(minA, X.Mid[0]); else minB = min(minB, X.Mid[0]); }
-        // records of up to 32 newcomers: fetched when they join, their
-        // successors' records prefetched once the segment is emitted
-        int4 nrec = make_int4(0, 0, 0, 0), ns4 = nrec;
-        int npref = 0;
+        // the previous segment's newcomers: their records have arrived,
+        // their successors' records are prefetched now
+        if (lane < npref) prefetch_succ(ws, ns4, nrec.z);
+        npref = 0;
         if (minA != INTMAX || minB != INTMAX) {
             const bool chooseRow = minA < minB;
             if (nm > 0 && chooseRow != rowLine) { dissolve(X, nm, rowLine); nm = 0; }
@@ -1404,16 +1430,22 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
         const int ns = nm + 1;
 
         // kseg identical batches: the leader, then the members in ascending id
-        const int64_t addm = (int64_t)kseg * ns;
+        // (a segment holds at most 2 048 batches of at most lineCap + 1 moves,
+        // so offsets within it fit 32 bits; the first-member field is the
+        // low 32 bits of the member count, as the ABI's int32 field holds it)
+        const int addm = kseg * ns;
         if (!overflow && nop + kseg <= cap_ops && nmem + addm <= cap_mem) {
-            for (int i = lane; i < kseg; i += 32) ops[nop + i] = rr_op{d, (int32_t)(nmem + (int64_t)i * ns), ns};
+            rr_op *op = ops + nop;
+            int32_t *mp = mem + nmem;
+            const int32_t f0 = (int32_t)nmem;
+            for (int i = lane; i < kseg; i += 32) op[i] = rr_op{d, f0 + i * ns, ns};
             if (ns == 1) {
-                for (int i = lane; i < kseg; i += 32) mem[nmem + i] = L;
+                for (int i = lane; i < kseg; i += 32) mp[i] = L;
             } else {
                 int u = small_mod(lane, ns);
                 const int step = small_mod(32, ns);
-                for (int64_t i = lane; i < addm; i += 32) {
-                    mem[nmem + i] = u == 0 ? L : X.Mid[u - 1];
+                for (int i = lane; i < addm; i += 32) {
+                    mp[i] = u == 0 ? L : X.Mid[u - 1];
                     u += step;
                     if (u >= ns) u -= ns;
                 }
@@ -1430,7 +1462,6 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
         // registers), then the members: finished members release their
         // successors, members whose leg ended leave the batch and become
         // statics, the others stay members.
-        if (lane < npref) prefetch_succ(ws, ns4, nrec.z);
         if (Ld.pref) {   // the leader's record has arrived by now
             prefetch_succ(ws, Ld.s4, lane == 0 ? Ld.nsu : 0);
             Ld.pref = false;
@@ -1531,7 +1562,17 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
             }
         }
         // the finished leader's successors, straight from its registers
-        if (lfin) {
+        if (lfin && Ld.nsu == 1 && (Ld.s4.x & SUCC_SINGLE)) {
+            // one successor, with no other predecessor: ready now (uniform)
+            const int sid = Ld.s4.x & SUCC_ID;
+            const int4 r = ws.rec[2 * sid];
+            if (sid == handId) { hand = 1; handRec = r; }
+            else {
+                const int si = alloc_slot(X, lane, 1, freeTop, ovfFreeTop, ovfUsed, hi, k, &err);
+                if (lane == 0 && si >= 0) push_both(X, si, fill_slot(X, si, sid, r));
+                __syncwarp();
+            }
+        } else if (lfin) {
             for (int e0 = 0; e0 < Ld.nsu; e0 += 32) {
                 const int e = e0 + lane;
                 const int32_t v = e == 0 ? Ld.s4.x : e == 1 ? Ld.s4.y : e == 2 ? Ld.s4.z : e == 3 ? Ld.s4.w
