@@ -1364,7 +1364,29 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
             }
             __syncwarp();
             // merge the newcomers into the sorted members (keys id << 32 | slot)
-            if (nc > 0) {
+            if (nc > 0 && nm <= 32 && nc <= 32) {
+                // the usual case, one member and one newcomer per lane: each
+                // newcomer's id is broadcast in turn; a member's rank grows by
+                // the newcomers below it, a newcomer's rank is the members
+                // below it (one vote) plus the newcomers below it (ids are
+                // distinct)
+                const int mId = lane < nm ? X.Mid[lane] : INTMAX;
+                const int mSl = lane < nm ? X.Msl[lane] : 0;
+                const long long kn = lane < nc ? X.Kb[lane] : 0ll;
+                const int nId = lane < nc ? (int)(kn >> 32) : INTMAX;
+                int rM = lane, rN = 0;
+                for (int j = 0; j < nc; ++j) {
+                    const int o = __shfl_sync(FULL, nId, j);
+                    rM += o < mId;
+                    rN += o < nId;
+                    const int below = __popc(__ballot_sync(FULL, mId < o));
+                    if (lane == j) rN += below;
+                }
+                __syncwarp();
+                if (lane < nm) { X.Mid[rM] = mId; X.Msl[rM] = mSl; }
+                if (lane < nc) { X.Mid[rN] = nId; X.Msl[rN] = (int)(kn & 0xffffffff); }
+                nm += nc;
+            } else if (nc > 0) {
                 const int tot = nm + nc;
                 long long *out = X.Kb + (lineCap + 2);
                 if (nc <= 32) {
