@@ -572,27 +572,35 @@ __device__ inline void s_gsweep_v(const Blk B, rr_instance *inst, JobWS *wsv, in
     }
 }
 
-// Distinct successors of one path, in first-occurrence order.
-template <class Emit>
-__device__ int distinct_succ(const int32_t *seq, int len, Emit emit)
+// Distinct successors of one path, in first-occurrence order, written to
+// out[0..) (each also counted in the successor's in-degree); returns their
+// number. Consecutive path vertices mostly share their next path, so most
+// entries repeat the previous one; a new value is checked against the first
+// four successors (registers) and then against the rest already written
+// (read back from out, which only this thread writes). The path's entries
+// are read 16 bytes at a time once aligned.
+__device__ inline int distinct_succ(const int32_t *seq, int len, int32_t *out, int32_t *indeg)
 {
     int cnt = 0;
-    int32_t buf[16];
-    int32_t last = -1;
-    for (int t = 0; t < len; ++t) {
-        const int32_t v = seq[t];
-        if (v < 0 || v == last) continue;
+    int32_t last = -1, b0 = -1, b1 = -1, b2 = -1, b3 = -1;
+    auto visit = [&](int32_t v) {
+        if (v < 0 || v == last) return;
         last = v;
-        bool seen = false;
-        const int lim = cnt < 16 ? cnt : 16;
-        for (int u = 0; u < lim; ++u) if (buf[u] == v) { seen = true; break; }
-        if (!seen && cnt >= 16)
-            for (int u = 0; u < t; ++u) if (seq[u] == v) { seen = true; break; }
-        if (seen) continue;
-        if (cnt < 16) buf[cnt] = v;
-        emit(cnt, v);
-        ++cnt;
+        if (v == b0 || v == b1 || v == b2 || v == b3) return;
+        for (int u = 4; u < cnt; ++u)
+            if (out[u] == v) return;
+        if (cnt == 0) b0 = v; else if (cnt == 1) b1 = v; else if (cnt == 2) b2 = v; else if (cnt == 3) b3 = v;
+        out[cnt++] = v;
+        atomicAdd(&indeg[v], 1);
+    };
+    int t = 0;
+    const int head = min(len, (int)((4u - (unsigned)(((uintptr_t)seq >> 2) & 3u)) & 3u));
+    for (; t < head; ++t) visit(seq[t]);
+    for (; t + 4 <= len; t += 4) {
+        const int4 q = *reinterpret_cast<const int4 *>(seq + t);
+        visit(q.x); visit(q.y); visit(q.z); visit(q.w);
     }
+    for (; t < len; ++t) visit(seq[t]);
     return cnt;
 }
 
@@ -606,11 +614,9 @@ __device__ inline void s_bsucc(const Blk B, rr_instance *inst, JobWS *wsv, int c
     if (!live(I)) return;
     JobWS &ws = wsv[q];
     const int64_t k = I->n_moves;
-    int32_t *indeg = ws.indeg;
     for (int64_t b = B.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)B.gx * blockDim.x) {
         const int lo = ws.pairOff[b], hi = ws.pairOff[b + 1];
-        int32_t *out = ws.succ + lo;
-        ws.succCnt[b] = distinct_succ(ws.nextAt + lo, hi - lo, [&](int u, int32_t s) { out[u] = s; atomicAdd(&indeg[s], 1); });
+        ws.succCnt[b] = distinct_succ(ws.nextAt + lo, hi - lo, ws.succ + lo, ws.indeg);
     }
 }
 
