@@ -57,7 +57,15 @@ __device__ inline void s_plan_setup(const Blk B, rr_instance *inst, JobWS *wsv, 
 
 // ------------------------------------------------- S0: load and transpose
 // Column-major bit columns: word w of column c holds rows 32w .. 32w+31.
-// bits32 input: a warp transposes a 32x32 bit tile with 32 ballots.
+// A warp takes a tile of 32 rows x 128 columns.
+// bits32 input: lane l reads row 32w + l, four words (128 columns) in one
+// 16-byte load when rows are 16-byte aligned (a row length of a multiple of
+// 128 columns and an aligned grid), else word by word; each of the four
+// 32x32 bit tiles is transposed with 32 ballots.
+// u8 input: lane l reads four consecutive bytes (columns 4l .. 4l+3 of the
+// tile) of each of the 32 rows in one 4-byte load when rows are 4-byte
+// aligned, else byte by byte, so that a warp reads 128 contiguous bytes per
+// row; the lane accumulates its four columns' words.
 __device__ inline void s_transpose(const Blk B, rr_instance *inst, JobWS *wsv, int count)
 {
     const int q = B.y;
@@ -65,31 +73,67 @@ __device__ inline void s_transpose(const Blk B, rr_instance *inst, JobWS *wsv, i
     const rr_instance *I = &inst[q];
     if (!live(I)) return;
     JobWS &ws = wsv[q];
-    const int m = I->m, n = I->n, W = (m + 31) >> 5, G = (n + 31) >> 5;
+    const int m = I->m, n = I->n, W = (m + 31) >> 5, G = (n + 31) >> 5, G4 = (n + 127) >> 7;
     const int lane = threadIdx.x & 31;
     const int nw = B.gx * (blockDim.x >> 5);
-    for (int item = B.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < G * W; item += nw) {
-        const int g = item / W, w = item % W;
-        const int col = 32 * g + lane;
-        uint32_t mine = 0;
-        if (I->layout == RR_BITS32) {
-            const uint32_t *src = (const uint32_t *)I->grid;
-            const int wpr = G, row = 32 * w + lane;
-            const uint32_t x = row < m ? src[(size_t)row * wpr + g] : 0u;
+    if (I->layout == RR_BITS32) {
+        const uint32_t *src = (const uint32_t *)I->grid;
+        const bool vec = (G & 3) == 0 && ((uintptr_t)src & 15) == 0;
+        for (int item = B.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < G4 * W; item += nw) {
+            const int g4 = item / W, w = item % W;
+            const int row = 32 * w + lane;
+            uint32_t x[4] = {0u, 0u, 0u, 0u};
+            if (row < m) {
+                const uint32_t *rp = src + (size_t)row * G + 4 * g4;
+                if (vec) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(rp);
+                    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+                } else {
 #pragma unroll
-            for (int b = 0; b < 32; ++b) {
-                const uint32_t v = __ballot_sync(FULL, (x >> b) & 1u);
-                if (b == lane) mine = v;
+                    for (int c = 0; c < 4; ++c)
+                        if (4 * g4 + c < G) x[c] = rp[c];
+                }
             }
-        } else {
-            const uint8_t *src = (const uint8_t *)I->grid;
-            if (col < n) {
-                const int rmax = min(32, m - 32 * w);
-                for (int r = 0; r < rmax; ++r)
-                    mine |= (uint32_t)(src[(size_t)(32 * w + r) * n + col] != 0) << r;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int g = 4 * g4 + c;
+                if (g >= G) break;
+                uint32_t mine = 0;
+#pragma unroll
+                for (int bt = 0; bt < 32; ++bt) {
+                    const uint32_t v = __ballot_sync(FULL, (x[c] >> bt) & 1u);
+                    if (bt == lane) mine = v;
+                }
+                const int col = 32 * g + lane;
+                if (col < n) ws.colbits[(size_t)col * W + w] = mine;
             }
         }
-        if (col < n) ws.colbits[(size_t)col * W + w] = mine;
+    } else {
+        const uint8_t *src = (const uint8_t *)I->grid;
+        const bool vec = (n & 3) == 0 && ((uintptr_t)src & 3) == 0;
+        for (int item = B.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < G4 * W; item += nw) {
+            const int g4 = item / W, w = item % W;
+            const int c0 = 128 * g4 + 4 * lane;
+            const int rmax = min(32, m - 32 * w);
+            uint32_t acc[4] = {0u, 0u, 0u, 0u};
+            if (c0 < n) {
+                for (int r = 0; r < rmax; ++r) {
+                    const uint8_t *rp = src + (size_t)(32 * w + r) * n + c0;
+                    if (vec) {
+                        const uint32_t v = *reinterpret_cast<const uint32_t *>(rp);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[c] |= (uint32_t)(((v >> (8 * c)) & 0xffu) != 0u) << r;
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (c0 + c < n) acc[c] |= (uint32_t)(rp[c] != 0) << r;
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c0 + c < n) ws.colbits[(size_t)(c0 + c) * W + w] = acc[c];
+        }
     }
 }
 
