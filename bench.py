@@ -22,6 +22,8 @@ from __future__ import annotations
 
 import argparse
 import concurrent.futures as cf
+import contextlib
+import gc
 import json
 import os
 import subprocess
@@ -40,6 +42,22 @@ import gridgen  # noqa: E402
 # hardware work queues would make them wait on one another (set before CUDA
 # initialises; it lasts for this process only).
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
+@contextlib.contextmanager
+def timed_region():
+    """Timed loops run with Python's cyclic garbage collector paused (after a
+    collection), so that a collection pass over the many small host objects of
+    the workload (descriptors, per-grid records) cannot stall the host between
+    kernel launches of a timed step."""
+    gc.collect()
+    was = gc.isenabled()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
+
 
 METRIC = "red-rec grids/s and p50/p99 plan latency, batched/served vs plain; %HBM roof"
 WORKLOAD = "4096 square grids, side U{32..256 step 16}, p U[0.5,0.7], centred floor(0.7*side) target, bits32"
@@ -389,18 +407,19 @@ def run_bird(args, rr, P, insts, grids, offs, sides, flush, cpu_threads):
     torch.cuda.synchronize()
     rr.rr_set_tracing(P.ctx, True)
     times, stage_tot = [], {}
-    for _ in range(args.steps):
-        flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        st = rr.rr_plan_batched(P.ctx, d_inst, count, max_side, flags, stream)
-        b.record(stream)
-        b.synchronize()
-        if st != rr.RR_OK:
-            raise rr.RRError(st, rr.rr_last_error(P.ctx))
-        times.append(a.elapsed_time(b))
-        for nm, ms in rr.rr_stage_times(P.ctx):
-            stage_tot[nm] = stage_tot.get(nm, 0.0) + ms
+    with timed_region():
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = rr.rr_plan_batched(P.ctx, d_inst, count, max_side, flags, stream)
+            b.record(stream)
+            b.synchronize()
+            if st != rr.RR_OK:
+                raise rr.RRError(st, rr.rr_last_error(P.ctx))
+            times.append(a.elapsed_time(b))
+            for nm, ms in rr.rr_stage_times(P.ctx):
+                stage_tot[nm] = stage_tot.get(nm, 0.0) + ms
     rr.rr_set_tracing(P.ctx, False)
     res = unpack_instances(d_inst, count)
     bad = [(g, x.status) for g, x in enumerate(res) if x.status not in (rr.RR_OK, rr.RR_INFEASIBLE)]
@@ -675,16 +694,17 @@ def run_ours(args, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step()
-        b.record(stream)
-        b.synchronize()
-        times.append(a.elapsed_time(b))
-        for nm, ms in rr.rr_stage_times(P.ctx):
-            stage_tot[nm] = stage_tot.get(nm, 0.0) + ms
+    with timed_region():
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            for nm, ms in rr.rr_stage_times(P.ctx):
+                stage_tot[nm] = stage_tot.get(nm, 0.0) + ms
     torch.cuda.synchronize()
     launches = rr.rr_launch_count(P.ctx) - launches0
     if world > 1:
@@ -701,14 +721,15 @@ def run_ours(args, rank, world, local):
         raise rr.RRError(-3, rr.rr_last_error(P.ctx))
     torch.cuda.synchronize()
     graph_ms = []
-    for _ in range(args.steps):
-        flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        rr.rr_plan_batched(P.ctx, d_inst, count, max_side, gflags, stream)
-        b.record(stream)
-        b.synchronize()
-        graph_ms.append(a.elapsed_time(b))
+    with timed_region():
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rr.rr_plan_batched(P.ctx, d_inst, count, max_side, gflags, stream)
+            b.record(stream)
+            b.synchronize()
+            graph_ms.append(a.elapsed_time(b))
     graph_total = float(sum(graph_ms))
 
     res = unpack_instances(d_inst, count)
@@ -767,12 +788,13 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for i in range(args.steps):
-        flush.fill_(1)
-        e2e_step(i)
-    b.record(copy_stream)
-    b.synchronize()
+    with timed_region():
+        a.record(stream)
+        for i in range(args.steps):
+            flush.fill_(1)
+            e2e_step(i)
+        b.record(copy_stream)
+        b.synchronize()
     torch.cuda.synchronize()
     e2e_total = max_over_ranks(a.elapsed_time(b), dev, world)
     last = bufs[(args.steps - 1) % 2]
