@@ -57,15 +57,16 @@ __device__ inline void s_plan_setup(const Blk B, rr_instance *inst, JobWS *wsv, 
 
 // ------------------------------------------------- S0: load and transpose
 // Column-major bit columns: word w of column c holds rows 32w .. 32w+31.
-// A warp takes a tile of 32 rows x 128 columns.
-// bits32 input: lane l reads row 32w + l, four words (128 columns) in one
-// 16-byte load when rows are 16-byte aligned (a row length of a multiple of
-// 128 columns and an aligned grid), else word by word; each of the four
-// 32x32 bit tiles is transposed with 32 ballots.
-// u8 input: lane l reads four consecutive bytes (columns 4l .. 4l+3 of the
-// tile) of each of the 32 rows in one 4-byte load when rows are 4-byte
-// aligned, else byte by byte, so that a warp reads 128 contiguous bytes per
-// row; the lane accumulates its four columns' words.
+// bits32 input, rows 16-byte aligned (a row length of a multiple of 128
+// columns and an aligned grid): a warp takes 32 rows x 128 columns, lane l
+// reads four words of row 32w + l in one 16-byte load, and each of the four
+// 32x32 bit tiles is transposed with 32 ballots. Other rows: a warp takes
+// one 32x32 tile, one word per lane.
+// u8 input, rows 4-byte aligned: a warp takes 32 rows x 128 columns, lane l
+// reads four consecutive bytes (columns 4l .. 4l+3) of each row in one
+// 4-byte load, so that a warp reads 128 contiguous bytes per row, and builds
+// its four columns' words. Other rows: lane l reads column 32g + l byte by
+// byte (32 contiguous bytes per row and warp).
 __device__ inline void s_transpose(const Blk B, rr_instance *inst, JobWS *wsv, int count)
 {
     const int q = B.y;
@@ -75,34 +76,38 @@ __device__ inline void s_transpose(const Blk B, rr_instance *inst, JobWS *wsv, i
     JobWS &ws = wsv[q];
     const int m = I->m, n = I->n, W = (m + 31) >> 5, G = (n + 31) >> 5, G4 = (n + 127) >> 7;
     const int lane = threadIdx.x & 31;
-    const int nw = B.gx * (blockDim.x >> 5);
+    const int w0 = B.x * (blockDim.x >> 5) + (threadIdx.x >> 5), nw = B.gx * (blockDim.x >> 5);
     if (I->layout == RR_BITS32) {
         const uint32_t *src = (const uint32_t *)I->grid;
-        const bool vec = (G & 3) == 0 && ((uintptr_t)src & 15) == 0;
-        for (int item = B.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < G4 * W; item += nw) {
-            const int g4 = item / W, w = item % W;
-            const int row = 32 * w + lane;
-            uint32_t x[4] = {0u, 0u, 0u, 0u};
-            if (row < m) {
-                const uint32_t *rp = src + (size_t)row * G + 4 * g4;
-                if (vec) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(rp);
-                    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-                } else {
+        if ((G & 3) == 0 && ((uintptr_t)src & 15) == 0) {
+            for (int item = w0; item < G4 * W; item += nw) {
+                const int g4 = item / W, w = item % W;
+                const int row = 32 * w + lane;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (row < m) v = *reinterpret_cast<const uint4 *>(src + (size_t)row * G + 4 * g4);
+                const uint32_t x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (4 * g4 + c < G) x[c] = rp[c];
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t mine = 0;
+#pragma unroll
+                    for (int bt = 0; bt < 32; ++bt) {
+                        const uint32_t bal = __ballot_sync(FULL, (x[c] >> bt) & 1u);
+                        if (bt == lane) mine = bal;
+                    }
+                    const int col = 32 * (4 * g4 + c) + lane;
+                    if (col < n) ws.colbits[(size_t)col * W + w] = mine;
                 }
             }
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int g = 4 * g4 + c;
-                if (g >= G) break;
+        } else {
+            for (int item = w0; item < G * W; item += nw) {
+                const int g = item / W, w = item % W;
+                const int row = 32 * w + lane;
+                const uint32_t x = row < m ? src[(size_t)row * G + g] : 0u;
                 uint32_t mine = 0;
 #pragma unroll
                 for (int bt = 0; bt < 32; ++bt) {
-                    const uint32_t v = __ballot_sync(FULL, (x[c] >> bt) & 1u);
-                    if (bt == lane) mine = v;
+                    const uint32_t bal = __ballot_sync(FULL, (x >> bt) & 1u);
+                    if (bt == lane) mine = bal;
                 }
                 const int col = 32 * g + lane;
                 if (col < n) ws.colbits[(size_t)col * W + w] = mine;
@@ -110,29 +115,37 @@ __device__ inline void s_transpose(const Blk B, rr_instance *inst, JobWS *wsv, i
         }
     } else {
         const uint8_t *src = (const uint8_t *)I->grid;
-        const bool vec = (n & 3) == 0 && ((uintptr_t)src & 3) == 0;
-        for (int item = B.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < G4 * W; item += nw) {
-            const int g4 = item / W, w = item % W;
-            const int c0 = 128 * g4 + 4 * lane;
-            const int rmax = min(32, m - 32 * w);
-            uint32_t acc[4] = {0u, 0u, 0u, 0u};
-            if (c0 < n) {
+        if ((n & 3) == 0 && ((uintptr_t)src & 3) == 0) {
+            for (int item = w0; item < G4 * W; item += nw) {
+                const int g4 = item / W, w = item % W;
+                const int c0 = 128 * g4 + 4 * lane;
+                if (c0 >= n) continue;
+                const int rmax = min(32, m - 32 * w);
+                const uint8_t *rp = src + (size_t)(32 * w) * n + c0;
+                uint32_t a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u;
                 for (int r = 0; r < rmax; ++r) {
-                    const uint8_t *rp = src + (size_t)(32 * w + r) * n + c0;
-                    if (vec) {
-                        const uint32_t v = *reinterpret_cast<const uint32_t *>(rp);
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[c] |= (uint32_t)(((v >> (8 * c)) & 0xffu) != 0u) << r;
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            if (c0 + c < n) acc[c] |= (uint32_t)(rp[c] != 0) << r;
-                    }
+                    const uint32_t v = *reinterpret_cast<const uint32_t *>(rp + (size_t)r * n);
+                    a0 |= (uint32_t)((v & 0xffu) != 0u) << r;
+                    a1 |= (uint32_t)((v & 0xff00u) != 0u) << r;
+                    a2 |= (uint32_t)((v & 0xff0000u) != 0u) << r;
+                    a3 |= (uint32_t)((v & 0xff000000u) != 0u) << r;
                 }
+                uint32_t *out = ws.colbits + (size_t)c0 * W + w;
+                out[0] = a0;
+                out[W] = a1;
+                out[2 * W] = a2;
+                out[3 * W] = a3;
             }
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (c0 + c < n) ws.colbits[(size_t)(c0 + c) * W + w] = acc[c];
+        } else {
+            for (int item = w0; item < G * W; item += nw) {
+                const int g = item / W, w = item % W;
+                const int col = 32 * g + lane;
+                if (col >= n) continue;
+                const int rmax = min(32, m - 32 * w);
+                uint32_t mine = 0;
+                for (int r = 0; r < rmax; ++r) mine |= (uint32_t)(src[(size_t)(32 * w + r) * n + col] != 0) << r;
+                ws.colbits[(size_t)col * W + w] = mine;
+            }
         }
     }
 }
