@@ -765,8 +765,15 @@ def run_ours(args, rank, world, local):
     h2d = host.numel() * 4 + bufs[0]["inst_h"].numel()
     d2h = bufs[0]["inst_h"].numel() + 4 * (4 * nm_ + 3 * no_ + ns_)
 
+    issued = []
+
     def e2e_step(i):
         B = bufs[i % 2]
+        # the host stays at most one step ahead: it issues step i once step
+        # i - 2's call has finished (queues stay shallow; step i - 1 keeps the
+        # GPU busy meanwhile)
+        if len(issued) >= 2:
+            issued[-2].synchronize()
         stream.wait_event(B["done"])            # that buffer set's previous copy back has finished
         grids.copy_(host, non_blocking=True)
         B["inst"].copy_(B["inst_h"], non_blocking=True)
@@ -775,6 +782,8 @@ def run_ours(args, rank, world, local):
             raise rr.RRError(st, rr.rr_last_error(P.ctx))
         called = torch.cuda.Event()
         called.record(stream)
+        issued.append(called)
+        del issued[:-2]
         copy_stream.wait_event(called)
         with torch.cuda.stream(copy_stream):
             B["back"].copy_(B["inst"], non_blocking=True)
