@@ -1,6 +1,7 @@
 """Host-side logic of bench.py (no GPU): the plain path's queueing model, the
 traffic ratio read from the committed ncu record, the batched-transfer count,
-the workload constructors and the per-rank seeds."""
+the workload constructors, the per-rank seeds and the garbage-collector pause of
+the timed loops."""
 import hashlib
 import json
 import os
@@ -98,3 +99,27 @@ def test_single_configs_match_the_named_sizes():
     assert sides == [32, 256, 1024]
     for name, side, t, lay in bench.SINGLE_CONFIGS:
         assert f"{side}x{side}" in name and f"{t}x{t}" in name and lay in ("u8", "bits32")
+
+
+def test_timed_region_pauses_the_garbage_collector():
+    """Timed loops run with Python's cyclic collector off; it is back on
+    afterwards, also when the loop raises."""
+    import gc
+    assert gc.isenabled()
+    with bench.timed_region():
+        assert not gc.isenabled()
+    assert gc.isenabled()
+    try:
+        with bench.timed_region():
+            raise RuntimeError("step failed")
+    except RuntimeError:
+        pass
+    assert gc.isenabled()
+    gc.disable()
+    try:
+        with bench.timed_region():
+            assert not gc.isenabled()
+        assert not gc.isenabled()      # a collector that was off stays off
+    finally:
+        gc.enable()
+
