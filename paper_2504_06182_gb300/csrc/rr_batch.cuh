@@ -654,8 +654,9 @@ __device__ inline void s_brec(const Blk B, rr_instance *inst, JobWS *wsv, int co
 
 // ---------------------------------------------------------- simulation
 //
-// The ready moves live in a slot table (structure of arrays; shared memory
-// up to its capacity, then a global overflow area with the same layout).
+// The ready moves other than the leader live in a slot table (structure of
+// arrays; shared memory up to its capacity, then a global overflow area with
+// the same layout); the leader is held in registers (LeaderState).
 // The moves of the current batch other than the leader ("members") are kept
 // in a persistent array sorted by id; every other ready move ("static") is
 // linked into two lists, one per (direction, row) and one per (direction,
