@@ -1445,9 +1445,24 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
         }
         // segment length: shortest remaining leg, next pickup
         int kseg = remL;
+        // up to 32 members: lane u keeps member u's slot, id, key, steps and
+        // leg end in registers from here through the advance
+        const bool regM = nm > 0 && nm <= 32;
+        int mSi = -1, mId = 0, mKey = 0, mT = 0, mLe = 0;
         if (nm > 0) {
             int remM = INTMAX;
-            for (int u = lane; u < nm; u += 32) { const int si = X.Msl[u]; remM = min(remM, SLOTF(X, legEnd, si) - SLOTF(X, t, si)); }
+            if (regM) {
+                if (lane < nm) {
+                    mSi = X.Msl[lane];
+                    mId = X.Mid[lane];
+                    mKey = SLOTF(X, key, mSi);
+                    mT = SLOTF(X, t, mSi);
+                    mLe = SLOTF(X, legEnd, mSi);
+                    remM = mLe - mT;
+                }
+            } else {
+                for (int u = lane; u < nm; u += 32) { const int si = X.Msl[u]; remM = min(remM, SLOTF(X, legEnd, si) - SLOTF(X, t, si)); }
+            }
             kseg = min(kseg, __reduce_min_sync(FULL, remM));   // one warp reduction
         }
         if (kseg > 1) {   // a static move of direction d the leader's line reaches
@@ -1467,10 +1482,10 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
             rr_op *op = ops + nop;
             int32_t *mp = mem + nmem;
             const int32_t f0 = (int32_t)nmem;
-            for (int i = lane; i < kseg; i += 32) op[i] = rr_op{d, f0 + i * ns, ns};
             if (ns == 1) {
-                for (int i = lane; i < kseg; i += 32) mp[i] = L;
+                for (int i = lane; i < kseg; i += 32) { op[i] = rr_op{d, f0 + i, 1}; mp[i] = L; }
             } else {
+                for (int i = lane; i < kseg; i += 32) op[i] = rr_op{d, f0 + i * ns, ns};
                 int u = small_mod(lane, ns);
                 const int step = small_mod(32, ns);
                 for (int i = lane; i < addm; i += 32) {
@@ -1521,10 +1536,10 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
             int si = -1, nsu = 0, newKey = 0, ov = 0;
             int4 fs4 = make_int4(0, 0, 0, 0);
             if (act) {
-                si = X.Msl[u];
-                const int key = SLOTF(X, key, si);
-                const int t = SLOTF(X, t, si) + kseg;
-                const int le = SLOTF(X, legEnd, si);
+                si = regM ? mSi : X.Msl[u];
+                const int key = regM ? mKey : SLOTF(X, key, si);
+                const int t = (regM ? mT : SLOTF(X, t, si)) + kseg;
+                const int le = regM ? mLe : SLOTF(X, legEnd, si);
                 int d_ = key_d(key);
                 const int r_ = key_r(key) + (d_ == 1 ? kseg : d_ == 0 ? -kseg : 0);
                 const int c_ = key_c(key) + (d_ == 3 ? kseg : d_ == 2 ? -kseg : 0);
@@ -1537,7 +1552,7 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
                     rem = iabs(dr - r_);
                 }
                 if (fin) {
-                    const int id = SLOTF(X, id, si);
+                    const int id = regM ? mId : SLOTF(X, id, si);
                     const int4 own = ws.rec[2 * id];
                     fs4 = ws.rec[2 * id + 1];
                     nsu = own.z;
@@ -1549,10 +1564,16 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
                     if (t + rem != le) SLOTF(X, legEnd, si) = (int16_t)(t + rem);
                 }
             }
-            // survivors keep their order (stable compaction into Kb)
+            // survivors keep their order (stable compaction: straight into the
+            // member arrays when they are held in registers, else into Kb)
             const bool keep = act && !fin && !turn;
             const unsigned kb = __ballot_sync(FULL, keep);
-            if (keep) X.Kb[nkeep + __popc(kb & lt)] = ((long long)X.Mid[u] << 32) | (unsigned)si;
+            if (regM) {
+                __syncwarp();
+                if (keep) { X.Mid[__popc(kb & lt)] = mId; X.Msl[__popc(kb & lt)] = si; }
+            } else if (keep) {
+                X.Kb[nkeep + __popc(kb & lt)] = ((long long)X.Mid[u] << 32) | (unsigned)si;
+            }
             nkeep += __popc(kb);
             // members whose leg ended become statics
             push_lanes(X, __ballot_sync(FULL, turn), si, newKey);
@@ -1610,7 +1631,8 @@ __device__ __forceinline__ void sim_body(const Blk B, rr_instance *inst, JobWS *
                               &err);
             }
         }
-        for (int u = lane; u < nkeep; u += 32) { X.Mid[u] = (int)(X.Kb[u] >> 32); X.Msl[u] = (int)(X.Kb[u] & 0xffffffff); }
+        if (!regM)
+            for (int u = lane; u < nkeep; u += 32) { X.Mid[u] = (int)(X.Kb[u] >> 32); X.Msl[u] = (int)(X.Kb[u] & 0xffffffff); }
         nm = nkeep;
         // a line moving across itself carries its index along
         if (rowLine && d < 2) lineIdx += sgn * kseg;
